@@ -1,0 +1,233 @@
+/*
+ * gbdbscan -- DBSCAN for 2D/3D fp32 points on one GB300 GPU (sm_103a).
+ *
+ * The method is FDbscan and FDbscan-DenseBox of "Fast tree-based algorithms
+ * for DBSCAN for low-dimensional data on GPUs" (Prokopenko, Lebrun-Grandie,
+ * Arndt; arXiv 2103.05162):
+ *   - the two-phase parallel disjoint-set DBSCAN (Sec. 3.2, Algorithm 3): a
+ *     preprocessing phase decides core points, a main phase unions every
+ *     eps-pair into a lock-free union-find as it is found, with no neighbour
+ *     list stored;
+ *   - a linear BVH over Morton-sorted primitives as the search index, each
+ *     pair visited once through the leaf-index mask (Sec. 4.1, Figure
+ *     "pair traversal");
+ *   - DenseBox: grid cells of side eps/sqrt(d) holding at least minPts points
+ *     become single leaves of the BVH whose points are all core and in one
+ *     cluster (Sec. 4.2);
+ *   - synchronisation-free union-find with path halving and a final
+ *     compression pass (Sec. 4.3).
+ *
+ * Definitions (Sec. 2.1). N_eps(x) = { y : dist(x,y) <= eps }, x included.
+ * x is core iff |N_eps(x)| >= minPts. Clusters are the connected components
+ * of the core points under the eps relation. A non-core point within eps of
+ * a core point is a border point and joins one of the clusters of its core
+ * neighbours (DBSCAN mode); in DBSCAN* mode border points are noise.
+ *
+ * Distance test. dist(x,y) <= eps is evaluated as the fp32 squared form with
+ * no fused multiply-add, in this order:
+ *   dk = fl(x_k - y_k); s = fl(d0*d0); s = fl(s + fl(dk*dk)), k = 1..d-1;
+ *   adjacent <=> s <= fl(eps*eps).
+ * The paper leaves the rounding open; fixing it makes results reproducible
+ * bit for bit.
+ *
+ * Output labels. labels_out[i] = -1 for noise, otherwise the smallest input
+ * index of a core point of i's cluster. Core points and noise are unique;
+ * a border point's cluster is any valid one.
+ *
+ * Conventions for every entry point:
+ *   - All functions are extern "C" and return dbscan_status (0 = OK).
+ *   - Arguments are checked before anything is enqueued; on error nothing is
+ *     enqueued and dbscan_last_error() holds a message (per host thread).
+ *   - Device pointers are owned by the caller, who keeps them alive until the
+ *     work on the stream (or the server job) has completed.
+ *   - Work is enqueued on the given stream (0 = the legacy default stream).
+ *     The library owns its device workspaces, one per (device, stream),
+ *     grown on demand and freed by dbscan_release_workspaces().
+ *   - Sizes: 0 <= n < 2^30 points; dim is 2 or 3; eps > 0 and finite;
+ *     min_pts >= 1.
+ */
+#ifndef GBDBSCAN_H
+#define GBDBSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DBSCAN_OK = 0,
+    DBSCAN_ERR_INVALID_ARG = 1,   /* a bad pointer, size or parameter */
+    DBSCAN_ERR_OOM = 2,           /* device or host allocation failed */
+    DBSCAN_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    DBSCAN_ERR_NONFINITE = 4,     /* an input coordinate is NaN or infinite */
+    DBSCAN_ERR_DEVICE_TIMEOUT = 5,/* a bounded device-side wait gave up */
+    DBSCAN_ERR_BUSY = 6,          /* server: no slot or budget free (try later) */
+    DBSCAN_ERR_NOT_FOUND = 7      /* server: unknown job id */
+} dbscan_status;
+
+typedef enum { DBSCAN_MODE_DBSCAN = 0, DBSCAN_MODE_DBSCAN_STAR = 1 } dbscan_mode;
+typedef enum { DBSCAN_ALGO_FDBSCAN = 0, DBSCAN_ALGO_DENSEBOX = 1 } dbscan_algo;
+
+/* opaque CUDA stream (cudaStream_t) */
+typedef void* dbscan_stream;
+
+/*
+ * Cluster n points (Sec. 3.2 Algorithm 3 with the index of Sec. 4.1 for
+ * algo = FDBSCAN, or of Sec. 4.2 for algo = DENSEBOX).
+ *   points      device, n*dim fp32, row-major (point i at points[i*dim..]).
+ *   labels_out  device, n int32: canonical label or -1 (see above).
+ *   core_out    device, n bytes (1 = core point) or NULL.
+ * The call enqueues the whole pipeline on `stream`. It waits on the host once,
+ * early, for the bounding box of the points (to size the grid and to report
+ * DBSCAN_ERR_NONFINITE before any clustering work); everything after that is
+ * asynchronous. A device-side timeout of the radix sort's bounded waits is
+ * reported by the next call on the same stream or by dbscan_stream_status().
+ */
+dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int min_pts,
+                         int mode, int algo, int32_t* labels_out, uint8_t* core_out,
+                         dbscan_stream stream);
+
+/*
+ * The same clustering on host buffers: copies points to the device, runs
+ * dbscan_run, copies labels (and core flags if core_out != NULL) back and
+ * waits for completion. Host buffers may be pageable or pinned (pinned is
+ * faster). Uses a library-owned device staging area per stream.
+ */
+dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts,
+                              int mode, int algo, int32_t* labels_host, uint8_t* core_host,
+                              dbscan_stream stream);
+
+/*
+ * Cluster `count` independent instances in one call (the batched workload).
+ *   points      device, concatenated instances; instance b is the rows
+ *               offsets[b] .. offsets[b+1]-1 of dims[b] floats each, i.e. its
+ *               first coordinate is at points + coord_offsets[b], where
+ *               coord_offsets[b] = sum_{c<b} (offsets[c+1]-offsets[c])*dims[c].
+ *   offsets     host, count+1 int64 row offsets (offsets[0] = 0, non-decreasing).
+ *   dims, eps, min_pts   host, per instance.
+ *   labels_out  device, offsets[count] int32; instance b's labels (relative to
+ *               the instance: 0 .. n_b-1, or -1) at labels_out + offsets[b].
+ *   core_out    device, offsets[count] bytes or NULL.
+ * Results are identical to calling dbscan_run per instance.
+ */
+dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, const int32_t* dims,
+                               const float* eps, const int32_t* min_pts, int32_t count, int mode,
+                               int algo, int32_t* labels_out, uint8_t* core_out, dbscan_stream stream);
+
+/*
+ * Serving: a request loop that admits clustering jobs as they arrive, by a
+ * device-memory budget and a slot limit, and runs admitted jobs concurrently
+ * on their own streams. Jobs keep their device state until collected.
+ *   dbscan_server_create   budget in bytes of device memory for job state;
+ *                          max_slots concurrent jobs (streams).
+ *   dbscan_server_submit   queues a job; points/labels_out/core_out are device
+ *                          pointers the caller keeps alive until the job is
+ *                          done. Returns DBSCAN_ERR_INVALID_ARG for bad
+ *                          arguments or jobs that can never fit the budget.
+ *   dbscan_server_poll     done_out = 1 once labels are complete; latency is
+ *                          seconds from submit to completion (0 while running).
+ *                          A finished job's status is returned by poll/wait.
+ *   dbscan_server_wait     blocks until the job is done.
+ *   dbscan_server_release  forgets a finished job (frees its id).
+ *   dbscan_server_destroy  drains all jobs, then frees everything.
+ */
+typedef struct dbscan_server dbscan_server;
+dbscan_status dbscan_server_create(size_t hbm_budget_bytes, int max_slots, dbscan_server** out);
+dbscan_status dbscan_server_submit(dbscan_server* srv, const float* points, int64_t n, int dim, float eps,
+                                   int min_pts, int mode, int algo, int32_t* labels_out, uint8_t* core_out,
+                                   uint64_t* job_id_out);
+dbscan_status dbscan_server_poll(dbscan_server* srv, uint64_t job_id, int* done_out, double* latency_s_out);
+dbscan_status dbscan_server_wait(dbscan_server* srv, uint64_t job_id);
+dbscan_status dbscan_server_release(dbscan_server* srv, uint64_t job_id);
+dbscan_status dbscan_server_destroy(dbscan_server* srv);
+
+/* Status of the last work enqueued by this library on `stream`: waits for the
+ * stream, then returns DBSCAN_ERR_DEVICE_TIMEOUT if a bounded device-side
+ * wait gave up (and clears the flag), else DBSCAN_OK. */
+dbscan_status dbscan_stream_status(dbscan_stream stream);
+
+/* Frees every cached device workspace (waits for their streams first). */
+dbscan_status dbscan_release_workspaces(void);
+
+/* Message of the last error returned on this host thread ("" if none). */
+const char* dbscan_last_error(void);
+
+/*
+ * Tuning knobs (process-wide): traversal block size in threads (a multiple of
+ * 32 up to 1024; 0 = default) and the DenseBox cell-side factor f in (0, 1]
+ * (cell side f*eps/sqrt(dim); 0 = default 1). Results do not depend on them.
+ */
+dbscan_status dbscan_set_tuning(int block_size, float cell_factor);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (not part of the method; for measurement)
+ * ------------------------------------------------------------------------- */
+
+/* Stages of one dbscan_run, in order: bounds, keys, sort, gather, leaves
+ * (DenseBox cells / tiles), lbvh (leaf boxes, topology, refit), init,
+ * preprocess, main, finalize. */
+#define DBSCAN_PROFILE_STAGES 10
+
+/* Process-wide switch: when on, every dbscan_run records a CUDA event pair
+ * around each stage on its stream (a few microseconds of overhead per run). */
+dbscan_status dbscan_profile_enable(int on);
+
+/* Waits for `stream`, then adds up the recorded stage times since the last
+ * collect: ms_out[DBSCAN_PROFILE_STAGES] milliseconds per stage and
+ * launches_out[DBSCAN_PROFILE_STAGES] (or NULL) the number of stage
+ * executions. Clears the records. */
+dbscan_status dbscan_profile_collect(dbscan_stream stream, double* ms_out, int64_t* launches_out);
+
+/* Name of stage i ("" if out of range). */
+const char* dbscan_profile_stage_name(int stage);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+int64_t dbscan_kernel_launches(void);
+
+/* Statistics of the last dbscan_run on `stream` (waits for it):
+ * stats_out[0] = number of BVH leaves m, stats_out[1] = number of grid cells
+ * (DenseBox; 0 for FDBSCAN). */
+dbscan_status dbscan_last_stats(dbscan_stream stream, int64_t* stats_out);
+
+/* ---------------------------------------------------------------------------
+ * Component entry points: the individual stages of the pipeline, exposed so
+ * that each can be used and tested on its own. All are asynchronous on
+ * `stream` and take device pointers.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
+ * the 64-bit keys (8-bit digits, one decoupled look-back pass per digit;
+ * the ordering of Morton codes in Sec. 4.1). keys/values are sorted in
+ * place; n < 2^30.
+ */
+dbscan_status dbscan_sort_pairs_u64(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
+                                    dbscan_stream stream);
+
+/*
+ * Morton codes (Sec. 4.1): each coordinate is mapped to an integer cell of a
+ * 2^bits-per-axis grid over [lo, hi] of that axis (cell = floor((x-lo) *
+ * (2^bits / (hi-lo))) clamped to [0, 2^bits-1]; 0 where hi == lo) and the
+ * cell indices are bit-interleaved with axis 0 in the lowest bit.
+ * dim*bits <= 64. lo/hi are host arrays of dim floats.
+ */
+dbscan_status dbscan_morton_codes(const float* points, int64_t n, int dim, const float* lo,
+                                  const float* hi, int bits, uint64_t* codes_out, dbscan_stream stream);
+
+/*
+ * Karras linear BVH topology (Sec. 4.1) over m >= 2 leaves with sorted keys
+ * (equal keys are ordered by leaf index). Internal node i (0 <= i < m-1) gets
+ * children_out[2i], children_out[2i+1] (a child c >= m-1 is leaf c-(m-1),
+ * otherwise internal node c), and range_out[2i], range_out[2i+1] = the first
+ * and last leaf index it covers. Node 0 is the root.
+ */
+dbscan_status dbscan_lbvh_topology(const uint64_t* leaf_keys, int64_t m, int32_t* children_out,
+                                   int32_t* range_out, dbscan_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBDBSCAN_H */

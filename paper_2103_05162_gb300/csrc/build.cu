@@ -1,0 +1,501 @@
+// Index construction: bounds, space-filling-curve keys, gather into sorted
+// order, DenseBox cell classification and leaf layout, Karras LBVH topology
+// and the atomic bottom-up refit (Sec. 4.1, 4.2).
+#include "build.cuh"
+
+namespace gbd {
+
+// ---------------------------------------------------------------------------
+// K1: exact fp32 bounding box of the points, plus a flag for NaN/Inf.
+// Each thread strides over the flat coordinate array with a stride that is a
+// multiple of D, so it always sees the same axis.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(BOUNDS_THREADS) k_bounds(const float* __restrict__ pts, int64_t n,
+                                                           uint32_t* __restrict__ ctrl)
+{
+    __shared__ uint32_t s_lo[D], s_hi[D];
+    __shared__ int s_bad;
+    if (threadIdx.x < D) { s_lo[threadIdx.x] = 0xffffffffu; s_hi[threadIdx.x] = 0u; }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const int64_t total = n * D;
+    const int64_t stride = (int64_t)gridDim.x * BOUNDS_THREADS;
+    const int axis = threadIdx.x % D;
+    float lo = INFINITY, hi = -INFINITY;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)BOUNDS_THREADS + threadIdx.x; i < total; i += stride) {
+        float v = __ldcs(pts + i);
+        bad |= !isfinite(v);
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    if (lo <= hi) {
+        atomicMin(&s_lo[axis], f2ord(lo));
+        atomicMax(&s_hi[axis], f2ord(hi));
+    }
+    if (bad) s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x < D) {
+        atomicMin(&ctrl[CTRL_LO + threadIdx.x], s_lo[threadIdx.x]);
+        atomicMax(&ctrl[CTRL_HI + threadIdx.x], s_hi[threadIdx.x]);
+    }
+    if (threadIdx.x == 0 && s_bad) atomicOr(&ctrl[CTRL_NONFINITE], 1u);
+}
+
+// ---------------------------------------------------------------------------
+// K2: keys. Bit interleaving with axis 0 in the lowest bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread2(uint64_t x)  // 32 bits -> even bits
+{
+    x &= 0xffffffffull;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+__device__ __forceinline__ uint64_t spread3(uint64_t x)  // 21 bits -> every third bit
+{
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+// floor'd cell coordinate -> index in [0, cmax] (clamped as an integer, so
+// that cmax is exact even where it is not representable in fp32)
+__device__ __forceinline__ uint32_t cell_index(float t, uint32_t cmax)
+{
+    const uint32_t c = (uint32_t)fminf(fmaxf(t, 0.0f), 4294967040.0f);
+    return c < cmax ? c : cmax;
+}
+
+template <int D>
+__device__ __forceinline__ uint64_t interleave(const uint32_t* c)
+{
+    if (D == 3) return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+    return spread2(c[0]) | (spread2(c[1]) << 1);
+}
+
+// Morton code of each point on a 2^bits grid over the (device-side) bounds;
+// u32 keys (FDBSCAN ordering). values = input index.
+template <int D>
+__global__ void k_morton32(const float* __restrict__ pts, int64_t n, const uint32_t* __restrict__ ctrl, int bits,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    float lo[D], scale[D];
+    const float cells = (float)(1u << bits);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        lo[k] = ord2f(ctrl[CTRL_LO + k]);
+        const float ext = __fsub_rn(ord2f(ctrl[CTRL_HI + k]), lo[k]);
+        scale[k] = ext > 0.0f ? __fdiv_rn(cells, ext) : 0.0f;
+    }
+    const uint32_t cmax = (1u << bits) - 1u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(pts[i * D + k], lo[k]), scale[k])), cmax);
+        }
+        keys[i] = (uint32_t)interleave<D>(c);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// Grid-cell key of each point (DenseBox, Sec. 4.2): cell index
+// floor((x_k - lo_k) * inv_h) clamped to [0, cmax_k], Morton-interleaved (or
+// packed axis by axis when `morton` is 0). values = input index.
+template <int D>
+__global__ void k_cellkey(const float* __restrict__ pts, int64_t n, GridParams g, uint64_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(pts[i * D + k], g.lo[k]), g.inv_h)), g.cmax[k]);
+        }
+        uint64_t key;
+        if (g.morton) {
+            key = interleave<D>(c);
+        } else {
+            key = 0;
+#pragma unroll
+            for (int k = D - 1; k >= 0; --k) key = (key << g.bits) | c[k];
+        }
+        keys[i] = key;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// generic Morton codes with host-side bounds (component entry point)
+template <int D>
+__global__ void k_morton_generic(const float* __restrict__ pts, int64_t n, GridParams g, uint64_t* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(pts[i * D + k], g.lo[k]), g.scale[k])), g.cmax[k]);
+        }
+        uint64_t key = 0;
+        for (int b = 0; b < g.bits; ++b)
+            for (int k = 0; k < D; ++k) key |= (uint64_t)((c[k] >> b) & 1u) << (b * D + k);
+        out[i] = key;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: gather the points into sorted order (structure of points, one 16-byte
+// (3D) or 8-byte (2D) record per point).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_gather(const float* __restrict__ pts, const uint32_t* __restrict__ perm, int64_t n,
+                         typename Traits<D>::Point* __restrict__ sp)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        sp[i] = Traits<D>::load_point(pts, perm[i]);
+}
+
+// ---------------------------------------------------------------------------
+// K5/K6: DenseBox classification. Cells are runs of equal keys in sorted
+// order. A cell is dense iff it holds at least minPts points AND the squared
+// distance between the corners of the exact bounding box of its points passes
+// the eps test: by monotone rounding every pair inside then passes too, so
+// "all points core and in one cluster" (Sec. 4.2) holds exactly, whatever
+// rounding the grid arithmetic suffered (the precision hazard of Sec. 4.2 is
+// turned into a per-cell check instead of an abort).
+// ---------------------------------------------------------------------------
+__global__ void k_cell_heads(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ head)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+// cellid = inclusive scan of head (1-based); writes cell starts and count
+__global__ void k_cell_starts(const int32_t* __restrict__ head, const int32_t* __restrict__ cellid, int64_t n,
+                              int32_t* __restrict__ cstart, uint32_t* __restrict__ ctrl)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (head[i]) cstart[cellid[i] - 1] = (int32_t)i;
+        if (i == n - 1) {
+            cstart[cellid[i]] = (int32_t)n;
+            ctrl[CTRL_NCELLS] = (uint32_t)cellid[i];
+        }
+    }
+}
+
+// one warp per candidate cell (count >= minPts): exact box and the guard
+template <int D>
+__global__ void k_cell_dense(const typename Traits<D>::Point* __restrict__ sp, const int32_t* __restrict__ cstart,
+                             const uint32_t* __restrict__ ctrl, int min_pts, float e2, uint8_t* __restrict__ cdense)
+{
+    using T = Traits<D>;
+    const int lane = threadIdx.x & 31;
+    const int64_t ncells = ctrl[CTRL_NCELLS];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = wid; c < ncells; c += nw) {
+        const int s = cstart[c], e = cstart[c + 1];
+        if (e - s < min_pts) {
+            if (lane == 0) cdense[c] = 0;
+            continue;
+        }
+        typename T::Box b = T::empty_box();
+        for (int j = s + lane; j < e; j += 32) T::grow(b, sp[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
+        if (lane == 0) cdense[c] = T::diag2(b) <= e2 ? 1 : 0;
+    }
+}
+
+// per point: dense flag and segment boundary marker (first point of a run of
+// non-dense points) for the max-scan
+__global__ void k_point_flags(const int32_t* __restrict__ cellid, const uint8_t* __restrict__ cdense, int64_t n,
+                              uint8_t* __restrict__ pdense, int32_t* __restrict__ bnd)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const bool d = cdense[cellid[i] - 1] != 0;
+        const bool prev_d = i > 0 ? cdense[cellid[i - 1] - 1] != 0 : true;
+        pdense[i] = d ? 1 : 0;
+        bnd[i] = (!d && prev_d) ? (int32_t)i : -1;
+    }
+}
+
+// leaf starts: the first point of every dense cell, and every TILE-th point of
+// each run of non-dense points (counted from the run's start)
+__global__ void k_leaf_flags(const int32_t* __restrict__ head, const uint8_t* __restrict__ pdense,
+                             const int32_t* __restrict__ segstart, int64_t n, int32_t* __restrict__ lf)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        lf[i] = pdense[i] ? head[i] : (((i - segstart[i]) % TILE) == 0 ? 1 : 0);
+}
+
+// lidx = exclusive scan of lf; writes leaf starts and m
+__global__ void k_leaf_write(const int32_t* __restrict__ lf, const int32_t* __restrict__ lidx, int64_t n,
+                             int32_t* __restrict__ lstart, uint32_t* __restrict__ ctrl)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (lf[i]) lstart[lidx[i]] = (int32_t)i;
+        if (i == n - 1) {
+            const int32_t m = lidx[i] + lf[i];
+            lstart[m] = (int32_t)n;
+            ctrl[CTRL_M] = (uint32_t)m;
+        }
+    }
+}
+
+// leaf records (start, end | dense << 31) and the leaf keys
+__global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t* __restrict__ pdense,
+                               const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ctrl,
+                               int2* __restrict__ leafr, uint64_t* __restrict__ lkey)
+{
+    const int64_t m = ctrl[CTRL_M];
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = lstart[l], e = lstart[l + 1];
+        const uint32_t dense = pdense[s];
+        leafr[l] = make_int2(s, (int32_t)((uint32_t)e | (dense << 31)));
+        lkey[l] = keys[s];
+    }
+}
+
+// FDBSCAN leaves: tiles of TILE consecutive sorted points
+__global__ void k_tile_records(const uint32_t* __restrict__ keys32, int64_t n, int64_t m, int2* __restrict__ leafr,
+                               uint64_t* __restrict__ lkey, uint32_t* __restrict__ ctrl)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = l * TILE;
+        const int64_t e = s + TILE < n ? s + TILE : n;
+        leafr[l] = make_int2((int32_t)s, (int32_t)e);
+        lkey[l] = keys32[s];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[CTRL_M] = (uint32_t)m;
+}
+
+// ---------------------------------------------------------------------------
+// Leaf boxes: exact min/max of each leaf's points (one warp per leaf), stored
+// at unified index (m-1) + l of the node-box array.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, const int2* __restrict__ leafr,
+                             const uint32_t* __restrict__ ctrl, typename Traits<D>::Box* __restrict__ nodebox)
+{
+    using T = Traits<D>;
+    const int lane = threadIdx.x & 31;
+    const int64_t m = ctrl[CTRL_M];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = wid; l < m; l += nw) {
+        const int2 r = leafr[l];
+        const int s = r.x, e = r.y & 0x7fffffff;
+        typename T::Box b = T::empty_box();
+        for (int j = s + lane; j < e; j += 32) T::grow(b, sp[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
+        if (lane == 0) nodebox[(m - 1) + l] = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: Karras (2012) LBVH topology. For internal node i the direction, the far
+// end of its range and the split come from the common-prefix length delta of
+// the sorted leaf keys; equal keys are told apart by the leaf index.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kdelta(const uint64_t* __restrict__ k, int64_t m, int64_t i, int64_t j)
+{
+    if (j < 0 || j >= m) return -1;
+    const uint64_t a = k[i], b = k[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__global__ void k_karras(const uint64_t* __restrict__ lkey, const uint32_t* __restrict__ ctrl, int64_t m_host,
+                         int4* __restrict__ nmeta, int32_t* __restrict__ parent, int2* __restrict__ child_out,
+                         int2* __restrict__ range_out)
+{
+    const int64_t m = m_host >= 0 ? m_host : (int64_t)ctrl[CTRL_M];
+    if (blockIdx.x == 0 && threadIdx.x == 0) parent[0] = -1;  // root (or the single leaf when m == 1)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m - 1; i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (kdelta(lkey, m, i, i + 1) - kdelta(lkey, m, i, i - 1)) > 0 ? 1 : -1;
+        const int dmin = kdelta(lkey, m, i, i - d);
+        int64_t lmax = 2;
+        while (kdelta(lkey, m, i, i + lmax * d) > dmin) lmax <<= 1;
+        int64_t l = 0;
+        for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+            if (kdelta(lkey, m, i, i + (l + t) * d) > dmin) l += t;
+        const int64_t j = i + l * d;
+        const int dnode = kdelta(lkey, m, i, j);
+        int64_t s = 0, t = l;
+        do {
+            t = (t + 1) >> 1;
+            if (kdelta(lkey, m, i, i + (s + t) * d) > dnode) s += t;
+        } while (t > 1);
+        const int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+        const int64_t first = i < j ? i : j, last = i < j ? j : i;
+        const int32_t left = (int32_t)(first == gamma ? (m - 1) + gamma : gamma);
+        const int32_t right = (int32_t)(last == gamma + 1 ? (m - 1) + gamma + 1 : gamma + 1);
+        nmeta[i] = make_int4(left, right, (int32_t)gamma, (int32_t)last);
+        parent[left] = (int32_t)i;
+        parent[right] = (int32_t)i;
+        if (child_out) child_out[i] = make_int2(left, right);
+        if (range_out) range_out[i] = make_int2((int32_t)first, (int32_t)last);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K8: bottom-up refit. One thread per leaf climbs towards the root; at each
+// parent the first thread to arrive stops and the second, which then knows
+// both children's boxes are final, merges them (exact min/max) and writes the
+// parent's node record. No thread ever waits.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__ parent,
+                        const int4* __restrict__ nmeta, typename Traits<D>::Box* nodebox,
+                        typename Traits<D>::Node* __restrict__ nodes, int32_t* visit)
+{
+    using T = Traits<D>;
+    using Box = typename T::Box;
+    const int64_t m = ctrl[CTRL_M];
+    uint32_t* ctrl_err = ctrl + CTRL_ERR;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+        int64_t idx = (m - 1) + l;
+        int32_t p = m > 1 ? parent[idx] : -1;
+        int depth = 0;
+        while (p >= 0) {
+            if (++depth > 128) {  // deeper than any valid tree: corrupt topology
+                atomicOr(&ctrl_err[0], ERR_STACK);
+                break;
+            }
+            __threadfence();
+            if (atomicAdd(&visit[p], 1) == 0) break;
+            __threadfence();
+            const int4 mt = nmeta[p];
+            Box L, R;
+            L.lo = __ldcg(&nodebox[mt.x].lo); L.hi = __ldcg(&nodebox[mt.x].hi);
+            R.lo = __ldcg(&nodebox[mt.y].lo); R.hi = __ldcg(&nodebox[mt.y].hi);
+            Box U = L;
+            T::merge(U, R);
+            __stcg(&nodebox[p].lo, U.lo);
+            __stcg(&nodebox[p].hi, U.hi);
+            nodes[p] = T::make_node(L, R, mt.x, mt.y, mt.z, mt.w);
+            idx = p;
+            p = parent[p];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned grid_for(int64_t work, int threads, int max_blocks)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStream_t s)
+{
+    const unsigned g = grid_for(n * dim, BOUNDS_THREADS, 152 * 8);
+    if (dim == 3) k_bounds<3><<<g, BOUNDS_THREADS, 0, s>>>(pts, n, ctrl);
+    else k_bounds<2><<<g, BOUNDS_THREADS, 0, s>>>(pts, n, ctrl);
+    note_launches(1);
+}
+
+void launch_morton32(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint32_t* keys,
+                     uint32_t* vals, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    if (dim == 3) k_morton32<3><<<g, 256, 0, s>>>(pts, n, ctrl, bits, keys, vals);
+    else k_morton32<2><<<g, 256, 0, s>>>(pts, n, ctrl, bits, keys, vals);
+    note_launches(1);
+}
+
+void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* keys, uint32_t* vals,
+                    cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    if (dim == 3) k_cellkey<3><<<g, 256, 0, s>>>(pts, n, gp, keys, vals);
+    else k_cellkey<2><<<g, 256, 0, s>>>(pts, n, gp, keys, vals);
+    note_launches(1);
+}
+
+void launch_morton_generic(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* out, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    if (dim == 3) k_morton_generic<3><<<g, 256, 0, s>>>(pts, n, gp, out);
+    else k_morton_generic<2><<<g, 256, 0, s>>>(pts, n, gp, out);
+    note_launches(1);
+}
+
+void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    if (dim == 3) k_gather<3><<<g, 256, 0, s>>>(pts, perm, n, static_cast<float4*>(sp));
+    else k_gather<2><<<g, 256, 0, s>>>(pts, perm, n, static_cast<float2*>(sp));
+    note_launches(1);
+}
+
+cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t n, int dim, int min_pts, float e2,
+                                   const DenseBoxTemps& t, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
+                                   cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    cudaError_t e;
+    k_cell_heads<<<g, 256, 0, s>>>(keys, n, t.head);
+    if ((e = scan_i32(t.head, t.cellid, n, SCAN_ADD, true, t.scan_temp, s)) != cudaSuccess) return e;
+    k_cell_starts<<<g, 256, 0, s>>>(t.head, t.cellid, n, t.cstart, ctrl);
+    const unsigned gw = 152 * 16;  // warps stride over cells
+    if (dim == 3)
+        k_cell_dense<3><<<gw, 256, 0, s>>>(static_cast<const float4*>(sp), t.cstart, ctrl, min_pts, e2, t.cdense);
+    else
+        k_cell_dense<2><<<gw, 256, 0, s>>>(static_cast<const float2*>(sp), t.cstart, ctrl, min_pts, e2, t.cdense);
+    k_point_flags<<<g, 256, 0, s>>>(t.cellid, t.cdense, n, t.pdense, t.bnd);
+    if ((e = scan_i32(t.bnd, t.segstart, n, SCAN_MAX, true, t.scan_temp, s)) != cudaSuccess) return e;
+    k_leaf_flags<<<g, 256, 0, s>>>(t.head, t.pdense, t.segstart, n, t.lf);
+    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
+    k_leaf_records<<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, leafr, lkey);
+    note_launches(7);
+    return cudaGetLastError();
+}
+
+void launch_tile_leaves(const uint32_t* keys32, int64_t n, int64_t m, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
+                        cudaStream_t s)
+{
+    k_tile_records<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(keys32, n, m, leafr, lkey, ctrl);
+    note_launches(1);
+}
+
+void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
+                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s)
+{
+    const unsigned gw = grid_for(m_cap * 32, 256, 152 * 16);
+    const unsigned g = grid_for(m_cap, 256, 152 * 16);
+    if (dim == 3) k_leaf_boxes<3><<<gw, 256, 0, s>>>(static_cast<const float4*>(sp), leafr, ctrl,
+                                                     static_cast<Traits<3>::Box*>(nodebox));
+    else k_leaf_boxes<2><<<gw, 256, 0, s>>>(static_cast<const float2*>(sp), leafr, ctrl,
+                                             static_cast<Traits<2>::Box*>(nodebox));
+    k_karras<<<g, 256, 0, s>>>(lkey, ctrl, -1, nmeta, parent, nullptr, nullptr);
+    cudaMemsetAsync(visit, 0, sizeof(int32_t) * (size_t)(m_cap > 1 ? m_cap - 1 : 1), s);
+    if (dim == 3) k_refit<3><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<Traits<3>::Box*>(nodebox),
+                                               static_cast<Traits<3>::Node*>(nodes), visit);
+    else k_refit<2><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<Traits<2>::Box*>(nodebox),
+                                       static_cast<Traits<2>::Node*>(nodes), visit);
+    note_launches(3);
+}
+
+void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* parent, int2* child_out,
+                        int2* range_out, cudaStream_t s)
+{
+    k_karras<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(lkey, nullptr, m, nmeta, parent, child_out, range_out);
+    note_launches(1);
+}
+
+}  // namespace gbd

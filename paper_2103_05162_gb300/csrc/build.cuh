@@ -1,0 +1,90 @@
+// Declarations shared by the pipeline stages (build.cu, traverse.cu, capi.cu).
+#pragma once
+
+#include "internal.cuh"
+
+namespace gbd {
+
+constexpr int BOUNDS_THREADS = 384;  // a multiple of 2 and 3
+
+// Slots of the per-workspace control block (uint32 words in device memory).
+enum : int {
+    CTRL_LO = 0,         // 3 words: order-preserving min per axis
+    CTRL_HI = 4,         // 3 words: order-preserving max per axis
+    CTRL_NONFINITE = 8,  // nonzero if a coordinate is NaN/Inf
+    CTRL_ERR = 9,        // device error bits (ERR_*)
+    CTRL_M = 10,         // number of BVH leaves
+    CTRL_NCELLS = 11,    // number of grid cells (DenseBox)
+    CTRL_WORK_PRE = 12,  // work counters of the persistent traversal kernels
+    CTRL_WORK_MAIN = 13,
+    CTRL_WORDS = 16
+};
+
+constexpr unsigned ERR_STACK = 2u;  // traversal/refit limits exceeded (cannot happen for valid trees)
+
+struct GridParams {
+    float lo[3];
+    float scale[3];     // per-axis scale (generic Morton codes)
+    float inv_h;        // 1 / cell side (DenseBox cells)
+    uint32_t cmax[3];   // largest cell index per axis
+    int bits;           // bits per axis in the key
+    int morton;         // 1: interleave, 0: pack axis by axis
+};
+
+struct DenseBoxTemps {
+    int32_t* head;      // n
+    int32_t* cellid;    // n
+    int32_t* cstart;    // n + 1
+    uint8_t* cdense;    // n
+    uint8_t* pdense;    // n
+    int32_t* bnd;       // n
+    int32_t* segstart;  // n
+    int32_t* lf;        // n
+    int32_t* lidx;      // n
+    int32_t* lstart;    // n + 1
+    int32_t* scan_temp; // scan_temp_words(n)
+};
+
+void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStream_t s);
+void launch_morton32(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint32_t* keys,
+                     uint32_t* vals, cudaStream_t s);
+void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* keys, uint32_t* vals,
+                    cudaStream_t s);
+void launch_morton_generic(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* out,
+                           cudaStream_t s);
+void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, cudaStream_t s);
+cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t n, int dim, int min_pts, float e2,
+                                   const DenseBoxTemps& t, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
+                                   cudaStream_t s);
+void launch_tile_leaves(const uint32_t* keys32, int64_t n, int64_t m, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
+                        cudaStream_t s);
+void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
+                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s);
+void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* parent, int2* child_out,
+                        int2* range_out, cudaStream_t s);
+
+// traverse.cu
+struct ClusterArgs {
+    const void* sp;        // sorted points
+    const void* nodes;     // m-1 node records
+    const void* nodebox;   // 2m-1 boxes (leaf boxes at m-1+l)
+    const int2* leafr;     // m leaf records
+    const uint32_t* perm;  // sorted position -> input index
+    int32_t* labels;       // n (union-find parents, sorted index space)
+    uint8_t* core;         // n (sorted order)
+    int32_t* canon;        // n (smallest input index per root)
+    uint32_t* ctrl;
+    int64_t n;
+    int64_t m_cap;         // upper bound of m (grid sizing)
+    int dim;
+    float e2;
+    int min_pts;
+    int mode;
+    int block;             // traversal block size
+};
+cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s);
+cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s);
+cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s);
+cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+
+}  // namespace gbd

@@ -1,0 +1,703 @@
+// The C ABI of libgbdbscan (include/gbdbscan.h): argument checks, per-stream
+// device workspaces and the enqueueing of the pipeline
+//   bounds -> keys -> radix sort -> gather -> [DenseBox cells] -> leaves ->
+//   LBVH topology -> refit -> union-find init -> [preprocessing] -> main ->
+//   finalize -> relabel
+// (Sec. 3.2 Algorithm 3 with the indexes of Sec. 4.1 / 4.2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "build.cuh"
+#include "capi_internal.h"
+
+namespace gbd {
+
+thread_local std::string t_err;
+
+dbscan_status set_error(dbscan_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+dbscan_status cuda_error(cudaError_t e, const char* what)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? DBSCAN_ERR_OOM : DBSCAN_ERR_CUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+#define TRY_CUDA(x)                                         \
+    do {                                                    \
+        cudaError_t e_ = (x);                               \
+        if (e_ != cudaSuccess) return cuda_error(e_, #x);   \
+    } while (0)
+
+Tuning g_tuning = {256, 1.0f};
+
+// ---------------------------------------------------------------------------
+// launch counting and opt-in per-stage timing (CUDA events on the stream)
+// ---------------------------------------------------------------------------
+static std::atomic<int64_t> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+static std::atomic<bool> g_profile{false};
+static const char* kStageNames[DBSCAN_PROFILE_STAGES] = {"bounds", "keys", "sort", "gather", "leaves",
+                                                         "lbvh", "init", "preprocess", "main", "finalize"};
+
+struct ProfState {
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+// records the start/end of one stage on the stream when profiling is on
+struct StageTimer {
+    Workspace* w;
+    cudaStream_t s;
+    bool on;
+    int stage = -1;
+    cudaEvent_t a = nullptr;
+    StageTimer(Workspace* w_, cudaStream_t s_) : w(w_), s(s_), on(g_profile.load()) {}
+    void begin(int st)
+    {
+        if (!on) return;
+        stage = st;
+        a = w->prof->get();
+        cudaEventRecord(a, s);
+    }
+    void end()
+    {
+        if (!on || stage < 0) return;
+        cudaEvent_t b = w->prof->get();
+        cudaEventRecord(b, s);
+        w->prof->recs.push_back({stage, a, b});
+        stage = -1;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += sizeof(T) * (count > 0 ? count : 1);
+        return p;
+    }
+};
+
+}  // namespace
+
+// Device buffers of one pipeline run, carved from the workspace arena.
+struct Plan {
+    uint32_t* ctrl;
+    void* keys;
+    void* keys_alt;
+    uint32_t* vals;
+    uint32_t* vals_alt;
+    uint32_t* hist;
+    uint32_t* counters;
+    uint32_t* status;
+    void* sp;
+    DenseBoxTemps db;
+    int2* leafr;
+    uint64_t* lkey;
+    void* nodebox;
+    void* nodes;
+    int4* nmeta;
+    int32_t* parent;
+    int32_t* visit;
+    int32_t* labels;
+    uint8_t* core;
+    int32_t* canon;
+};
+
+int64_t leaf_cap(int64_t n, int algo) { return algo == DBSCAN_ALGO_FDBSCAN ? (n + TILE - 1) / TILE : n; }
+
+size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
+{
+    Carver c(base);
+    const int64_t mc = leaf_cap(n, algo);
+    const size_t pt = dim == 3 ? sizeof(float4) : sizeof(float2);
+    const size_t box = dim == 3 ? sizeof(Traits<3>::Box) : sizeof(Traits<2>::Box);
+    const size_t node = dim == 3 ? sizeof(Traits<3>::Node) : sizeof(Traits<2>::Node);
+    p.ctrl = c.take<uint32_t>(CTRL_WORDS);
+    p.keys = c.take<uint64_t>(n);
+    p.keys_alt = c.take<uint64_t>(n);
+    p.vals = c.take<uint32_t>(n);
+    p.vals_alt = c.take<uint32_t>(n);
+    p.hist = c.take<uint32_t>(8 * 256);
+    p.counters = c.take<uint32_t>(8);
+    p.status = c.take<uint32_t>(sort_status_words(n, 8, 64));
+    p.sp = c.take<char>(pt * (size_t)n);
+    if (algo == DBSCAN_ALGO_DENSEBOX) {
+        p.db.head = c.take<int32_t>(n);
+        p.db.cellid = c.take<int32_t>(n);
+        p.db.cstart = c.take<int32_t>(n + 1);
+        p.db.cdense = c.take<uint8_t>(n);
+        p.db.pdense = c.take<uint8_t>(n);
+        p.db.bnd = c.take<int32_t>(n);
+        p.db.segstart = c.take<int32_t>(n);
+        p.db.lf = c.take<int32_t>(n);
+        p.db.lidx = c.take<int32_t>(n);
+        p.db.lstart = c.take<int32_t>(n + 1);
+        p.db.scan_temp = c.take<int32_t>(scan_temp_words(n));
+    } else {
+        p.db = DenseBoxTemps{};
+    }
+    p.leafr = c.take<int2>(mc);
+    p.lkey = c.take<uint64_t>(mc);
+    p.nodebox = c.take<char>(box * (size_t)(2 * mc));
+    p.nodes = c.take<char>(node * (size_t)mc);
+    p.nmeta = c.take<int4>(mc);
+    p.parent = c.take<int32_t>(2 * mc);
+    p.visit = c.take<int32_t>(mc);
+    p.labels = c.take<int32_t>(n);
+    p.core = c.take<uint8_t>(n);
+    p.canon = c.take<int32_t>(n);
+    return c.off + 256;
+}
+
+size_t workspace_bytes(int64_t n, int dim, int algo)
+{
+    Plan p;
+    return carve_plan(p, nullptr, n, dim, algo);
+}
+
+// ---------------------------------------------------------------------------
+// per (device, stream) workspaces
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
+
+}  // namespace
+
+Workspace* get_workspace(cudaStream_t s)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    auto key = std::make_pair(dev, s);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) return it->second;
+    Workspace* w = new Workspace();
+    w->device = dev;
+    w->stream = s;
+    if (cudaMallocHost(&w->ctrl_host, CTRL_WORDS * sizeof(uint32_t)) != cudaSuccess) {
+        delete w;
+        return nullptr;
+    }
+    memset(w->ctrl_host, 0, CTRL_WORDS * sizeof(uint32_t));
+    w->prof = new ProfState();
+    g_ws[key] = w;
+    return w;
+}
+
+cudaError_t ensure_arena(Arena& a, size_t bytes, cudaStream_t s)
+{
+    if (a.cap >= bytes) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (a.base) cudaFree(a.base);
+    a.base = nullptr;
+    a.cap = 0;
+    size_t want = bytes + bytes / 8;  // headroom against regrowth
+    e = cudaMalloc(&a.base, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&a.base, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return cudaErrorMemoryAllocation; }
+        want = bytes;
+    }
+    a.cap = want;
+    // the control block (first words of every arena layout) starts cleared
+    return cudaMemsetAsync(a.base, 0, 256, s);
+}
+
+void release_stream_workspace(cudaStream_t s)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Workspace* w = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_ws_mu);
+        auto it = g_ws.find(std::make_pair(dev, s));
+        if (it == g_ws.end()) return;
+        w = it->second;
+        g_ws.erase(it);
+    }
+    free_workspace(w);
+}
+
+void free_workspace(Workspace* w)
+{
+    cudaStreamSynchronize(w->stream);
+    if (w->main.base) cudaFree(w->main.base);
+    if (w->aux.base) cudaFree(w->aux.base);
+    if (w->io.base) cudaFree(w->io.base);
+    if (w->ctrl_host) cudaFreeHost(w->ctrl_host);
+    if (w->prof) {
+        for (auto& r : w->prof->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : w->prof->pool) cudaEventDestroy(e);
+        delete w->prof;
+    }
+    delete w;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+dbscan_status check_run_args(const void* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
+                             const void* labels_out)
+{
+    if (n < 0 || n >= (int64_t(1) << 30)) return set_error(DBSCAN_ERR_INVALID_ARG, "n = %lld out of range [0, 2^30)", (long long)n);
+    if (dim != 2 && dim != 3) return set_error(DBSCAN_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", dim);
+    if (!(eps > 0.0f) || !std::isfinite(eps)) return set_error(DBSCAN_ERR_INVALID_ARG, "eps must be positive and finite");
+    if (min_pts < 1) return set_error(DBSCAN_ERR_INVALID_ARG, "min_pts must be >= 1 (got %d)", min_pts);
+    if (mode != DBSCAN_MODE_DBSCAN && mode != DBSCAN_MODE_DBSCAN_STAR)
+        return set_error(DBSCAN_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (algo != DBSCAN_ALGO_FDBSCAN && algo != DBSCAN_ALGO_DENSEBOX)
+        return set_error(DBSCAN_ERR_INVALID_ARG, "unknown algo %d", algo);
+    if (n > 0 && (!points || !labels_out)) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
+    return DBSCAN_OK;
+}
+
+// DenseBox grid: cell side f * eps / sqrt(dim) (Sec. 4.2), coarsened when the
+// cell count per axis would exceed the key width (the per-cell guard keeps
+// the result exact for any cell size).
+GridParams densebox_grid(const float* lo, const float* hi, int dim, float eps, float factor, int* key_bits)
+{
+    GridParams g{};
+    double h = (double)factor * (double)eps / std::sqrt((double)dim);
+    const int maxbits = dim == 3 ? 21 : 31;
+    const double maxcells = std::ldexp(1.0, maxbits);
+    double ext_max = 0.0;
+    for (int k = 0; k < dim; ++k) ext_max = std::fmax(ext_max, (double)hi[k] - (double)lo[k]);
+    if (ext_max / h >= maxcells - 2.0) h = ext_max / (maxcells - 2.0);
+    const float inv_h = (float)(1.0 / h);
+    int bits = 1;
+    for (int k = 0; k < dim; ++k) {
+        g.lo[k] = lo[k];
+        double c = std::floor(((double)hi[k] - (double)lo[k]) * (double)inv_h) + 1.0;
+        if (c > maxcells - 1.0) c = maxcells - 1.0;
+        g.cmax[k] = (uint32_t)c;  // one spare cell for rounding at the top
+        while (bits < maxbits && (std::ldexp(1.0, bits) - 1.0) < (double)g.cmax[k]) ++bits;
+    }
+    g.inv_h = inv_h;
+    g.bits = bits;
+    g.morton = 1;
+    *key_bits = bits * dim;
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// the pipeline
+// ---------------------------------------------------------------------------
+enum Stage { ST_BOUNDS, ST_KEYS, ST_SORT, ST_GATHER, ST_LEAVES, ST_LBVH, ST_INIT, ST_PRE, ST_MAIN, ST_FINAL };
+dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                           int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
+{
+    TRY_CUDA(ensure_arena(w->main, workspace_bytes(n, dim, algo), s));
+    Plan p;
+    carve_plan(p, w->main.base, n, dim, algo);
+
+    StageTimer T(w, s);
+    // K1 bounds, then one host wait for them
+    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, 4 * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, 5 * sizeof(uint32_t), s));
+    T.begin(ST_BOUNDS);
+    launch_bounds(points, n, dim, p.ctrl, s);
+    T.end();
+    TRY_CUDA(cudaGetLastError());
+    TRY_CUDA(cudaMemcpyAsync(w->ctrl_host, p.ctrl, CTRL_WORDS * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    const uint32_t* hc = w->ctrl_host;
+    if (hc[CTRL_ERR] != 0) {
+        TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_ERR, 0, sizeof(uint32_t), s));
+        return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "earlier work on this stream reported device error bits 0x%x",
+                         hc[CTRL_ERR]);
+    }
+    if (hc[CTRL_NONFINITE] != 0) return set_error(DBSCAN_ERR_NONFINITE, "input coordinates contain NaN or Inf");
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        lo[k] = ord2f(hc[CTRL_LO + k]);
+        hi[k] = ord2f(hc[CTRL_HI + k]);
+    }
+    const float e2 = eps * eps;
+
+    SortBuffers sb;
+    sb.keys_alt = p.keys_alt;
+    sb.vals_alt = p.vals_alt;
+    sb.hist = p.hist;
+    sb.status = p.status;
+    sb.counters = p.counters;
+    sb.err = p.ctrl + CTRL_ERR;
+    bool in_alt = false;
+    int64_t m_cap = leaf_cap(n, algo);
+    const uint32_t* perm = nullptr;
+
+    if (algo == DBSCAN_ALGO_FDBSCAN) {
+        const int bits = dim == 3 ? 10 : 16;
+        uint32_t* k32 = static_cast<uint32_t*>(p.keys);
+        T.begin(ST_KEYS);
+        launch_morton32(points, n, dim, p.ctrl, bits, k32, p.vals, s);
+        T.end();
+        T.begin(ST_SORT);
+        TRY_CUDA(sort_pairs_u32(k32, p.vals, n, bits * dim, sb, s, &in_alt));
+        T.end();
+        const uint32_t* keys_sorted = in_alt ? static_cast<uint32_t*>(p.keys_alt) : k32;
+        perm = in_alt ? p.vals_alt : p.vals;
+        T.begin(ST_GATHER);
+        launch_gather(points, perm, n, dim, p.sp, s);
+        T.end();
+        T.begin(ST_LEAVES);
+        launch_tile_leaves(keys_sorted, n, m_cap, p.leafr, p.lkey, p.ctrl, s);
+        T.end();
+    } else {
+        int key_bits = 0;
+        GridParams g = densebox_grid(lo, hi, dim, eps, g_tuning.cell_factor, &key_bits);
+        uint64_t* k64 = static_cast<uint64_t*>(p.keys);
+        T.begin(ST_KEYS);
+        launch_cellkey(points, n, dim, g, k64, p.vals, s);
+        T.end();
+        T.begin(ST_SORT);
+        TRY_CUDA(sort_pairs_u64(k64, p.vals, n, key_bits, sb, s, &in_alt));
+        T.end();
+        const uint64_t* keys_sorted = in_alt ? static_cast<uint64_t*>(p.keys_alt) : k64;
+        perm = in_alt ? p.vals_alt : p.vals;
+        T.begin(ST_GATHER);
+        launch_gather(points, perm, n, dim, p.sp, s);
+        T.end();
+        T.begin(ST_LEAVES);
+        TRY_CUDA(launch_densebox_leaves(keys_sorted, p.sp, n, dim, min_pts, e2, p.db, p.leafr, p.lkey, p.ctrl, s));
+        T.end();
+    }
+    TRY_CUDA(cudaGetLastError());
+    T.begin(ST_LBVH);
+    launch_lbvh(p.sp, dim, p.leafr, p.lkey, m_cap, p.ctrl, p.nmeta, p.parent, p.visit, p.nodebox, p.nodes, s);
+    T.end();
+    TRY_CUDA(cudaGetLastError());
+
+    ClusterArgs a;
+    a.sp = p.sp;
+    a.nodes = p.nodes;
+    a.nodebox = p.nodebox;
+    a.leafr = p.leafr;
+    a.perm = perm;
+    a.labels = p.labels;
+    a.core = p.core;
+    a.canon = p.canon;
+    a.ctrl = p.ctrl;
+    a.n = n;
+    a.m_cap = m_cap;
+    a.dim = dim;
+    a.e2 = e2;
+    a.min_pts = min_pts;
+    a.mode = mode;
+    a.block = g_tuning.block;
+    T.begin(ST_INIT);
+    TRY_CUDA(launch_cluster_init(a, s));
+    T.end();
+    if (min_pts > 2) {
+        T.begin(ST_PRE);
+        TRY_CUDA(launch_cluster_pre(a, s));
+        T.end();
+    }
+    T.begin(ST_MAIN);
+    TRY_CUDA(launch_cluster_main(a, s));
+    T.end();
+    T.begin(ST_FINAL);
+    TRY_CUDA(launch_cluster_final(a, labels_out, core_out, s));
+    T.end();
+    return DBSCAN_OK;
+}
+
+}  // namespace gbd
+
+using namespace gbd;
+
+extern "C" {
+
+dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
+                         int32_t* labels_out, uint8_t* core_out, dbscan_stream stream)
+{
+    t_err.clear();
+    dbscan_status st = check_run_args(points, n, dim, eps, min_pts, mode, algo, labels_out);
+    if (st != DBSCAN_OK) return st;
+    if (n == 0) return DBSCAN_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    return run_pipeline(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+}
+
+dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,
+                              int algo, int32_t* labels_host, uint8_t* core_host, dbscan_stream stream)
+{
+    t_err.clear();
+    dbscan_status st = check_run_args(points_host, n, dim, eps, min_pts, mode, algo, labels_host);
+    if (st != DBSCAN_OK) return st;
+    if (n == 0) return DBSCAN_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    const size_t pbytes = sizeof(float) * (size_t)n * dim;
+    const size_t lbytes = sizeof(int32_t) * (size_t)n;
+    const size_t io = ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)) + (size_t)n + 256;
+    TRY_CUDA(ensure_arena(w->io, io, s));
+    char* base = static_cast<char*>(w->io.base);
+    float* dpts = reinterpret_cast<float*>(base);
+    int32_t* dlab = reinterpret_cast<int32_t*>(base + ((pbytes + 255) & ~size_t(255)));
+    uint8_t* dcore = reinterpret_cast<uint8_t*>(base + ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)));
+    TRY_CUDA(cudaMemcpyAsync(dpts, points_host, pbytes, cudaMemcpyHostToDevice, s));
+    st = run_pipeline(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
+    if (st != DBSCAN_OK) return st;
+    TRY_CUDA(cudaMemcpyAsync(labels_host, dlab, lbytes, cudaMemcpyDeviceToHost, s));
+    if (core_host) TRY_CUDA(cudaMemcpyAsync(core_host, dcore, (size_t)n, cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, const int32_t* dims, const float* eps,
+                               const int32_t* min_pts, int32_t count, int mode, int algo, int32_t* labels_out,
+                               uint8_t* core_out, dbscan_stream stream)
+{
+    t_err.clear();
+    if (count < 0) return set_error(DBSCAN_ERR_INVALID_ARG, "count must be >= 0");
+    if (count == 0) return DBSCAN_OK;
+    if (!offsets || !dims || !eps || !min_pts) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
+    if (offsets[0] != 0) return set_error(DBSCAN_ERR_INVALID_ARG, "offsets[0] must be 0");
+    int64_t coords = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        if (nb < 0) return set_error(DBSCAN_ERR_INVALID_ARG, "offsets must be non-decreasing (instance %d)", b);
+        dbscan_status st = check_run_args(points, nb, dims[b], eps[b], min_pts[b], mode, algo, labels_out);
+        if (st != DBSCAN_OK) return set_error(st, "instance %d: %s", b, t_err.c_str());
+        coords += nb * dims[b];
+    }
+    if (offsets[count] >= (int64_t(1) << 31)) return set_error(DBSCAN_ERR_INVALID_ARG, "too many points in total");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    int64_t coff = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        if (nb > 0) {
+            dbscan_status st = run_pipeline(w, points + coff, nb, dims[b], eps[b], min_pts[b], mode, algo,
+                                            labels_out + offsets[b], core_out ? core_out + offsets[b] : nullptr, s);
+            if (st != DBSCAN_OK) return st;
+        }
+        coff += nb * dims[b];
+    }
+    (void)coords;
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_stream_status(dbscan_stream stream)
+{
+    t_err.clear();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY_CUDA(cudaStreamSynchronize(s));
+    Workspace* w = get_workspace(s);
+    if (!w || !w->main.base) return DBSCAN_OK;
+    uint32_t err = 0;
+    Plan p;
+    carve_plan(p, w->main.base, 0, 3, DBSCAN_ALGO_FDBSCAN);
+    TRY_CUDA(cudaMemcpy(&err, p.ctrl + CTRL_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (err) {
+        TRY_CUDA(cudaMemset(p.ctrl + CTRL_ERR, 0, sizeof(uint32_t)));
+        return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "device error bits 0x%x", err);
+    }
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_release_workspaces(void)
+{
+    t_err.clear();
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    for (auto& kv : g_ws) free_workspace(kv.second);
+    g_ws.clear();
+    return DBSCAN_OK;
+}
+
+const char* dbscan_last_error(void) { return t_err.c_str(); }
+
+dbscan_status dbscan_profile_enable(int on)
+{
+    g_profile.store(on != 0);
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_profile_collect(dbscan_stream stream, double* ms_out, int64_t* launches_out)
+{
+    t_err.clear();
+    if (!ms_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null ms_out");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY_CUDA(cudaStreamSynchronize(s));
+    Workspace* w = get_workspace(s);
+    for (int i = 0; i < DBSCAN_PROFILE_STAGES; ++i) {
+        ms_out[i] = 0.0;
+        if (launches_out) launches_out[i] = 0;
+    }
+    if (!w) return DBSCAN_OK;
+    for (auto& r : w->prof->recs) {
+        float ms = 0.f;
+        TRY_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        ms_out[r.stage] += ms;
+        if (launches_out) launches_out[r.stage] += 1;
+        w->prof->pool.push_back(r.a);
+        w->prof->pool.push_back(r.b);
+    }
+    w->prof->recs.clear();
+    return DBSCAN_OK;
+}
+
+const char* dbscan_profile_stage_name(int stage)
+{
+    return (stage >= 0 && stage < DBSCAN_PROFILE_STAGES) ? kStageNames[stage] : "";
+}
+
+int64_t dbscan_kernel_launches(void) { return launches_so_far(); }
+
+dbscan_status dbscan_last_stats(dbscan_stream stream, int64_t* stats_out)
+{
+    t_err.clear();
+    if (!stats_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null stats_out");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY_CUDA(cudaStreamSynchronize(s));
+    Workspace* w = get_workspace(s);
+    stats_out[0] = stats_out[1] = 0;
+    if (!w || !w->main.base) return DBSCAN_OK;
+    uint32_t ctrl[CTRL_WORDS];
+    TRY_CUDA(cudaMemcpy(ctrl, w->main.base, sizeof(ctrl), cudaMemcpyDeviceToHost));
+    stats_out[0] = ctrl[CTRL_M];
+    stats_out[1] = ctrl[CTRL_NCELLS];
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_set_tuning(int block_size, float cell_factor)
+{
+    t_err.clear();
+    if (block_size != 0 && (block_size < 32 || block_size > 1024 || block_size % 32 != 0))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "block size must be a multiple of 32 in [32, 1024]");
+    if (cell_factor != 0.0f && !(cell_factor > 0.0f && cell_factor <= 1.0f))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "cell factor must be in (0, 1]");
+    g_tuning.block = block_size ? block_size : 256;
+    g_tuning.cell_factor = cell_factor != 0.0f ? cell_factor : 1.0f;
+    return DBSCAN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// component entry points
+// ---------------------------------------------------------------------------
+dbscan_status dbscan_sort_pairs_u64(uint64_t* keys, uint32_t* values, int64_t n, int key_bits, dbscan_stream stream)
+{
+    t_err.clear();
+    if (n < 0 || n >= (int64_t(1) << 30)) return set_error(DBSCAN_ERR_INVALID_ARG, "n out of range");
+    if (key_bits < 0 || key_bits > 64) return set_error(DBSCAN_ERR_INVALID_ARG, "key_bits must be in [0, 64]");
+    if (n > 0 && (!keys || !values)) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
+    if (n <= 1 || key_bits == 0) return DBSCAN_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    Carver c(nullptr);
+    c.take<uint64_t>(n); c.take<uint32_t>(n); c.take<uint32_t>(8 * 256); c.take<uint32_t>(8);
+    c.take<uint32_t>(sort_status_words(n, 8, key_bits)); c.take<uint32_t>(CTRL_WORDS);
+    TRY_CUDA(ensure_arena(w->aux, c.off + 256, s));
+    Carver d(w->aux.base);
+    SortBuffers sb;
+    sb.keys_alt = d.take<uint64_t>(n);
+    sb.vals_alt = d.take<uint32_t>(n);
+    sb.hist = d.take<uint32_t>(8 * 256);
+    sb.counters = d.take<uint32_t>(8);
+    sb.status = d.take<uint32_t>(sort_status_words(n, 8, key_bits));
+    uint32_t* ctrl = d.take<uint32_t>(CTRL_WORDS);
+    sb.err = ctrl + CTRL_ERR;
+    TRY_CUDA(cudaMemsetAsync(ctrl, 0, CTRL_WORDS * sizeof(uint32_t), s));
+    bool in_alt = false;
+    TRY_CUDA(sort_pairs_u64(keys, values, n, key_bits, sb, s, &in_alt));
+    if (in_alt) {
+        TRY_CUDA(cudaMemcpyAsync(keys, sb.keys_alt, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        TRY_CUDA(cudaMemcpyAsync(values, sb.vals_alt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    uint32_t err = 0;
+    TRY_CUDA(cudaMemcpyAsync(&err, ctrl + CTRL_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (err) return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "radix sort look-back gave up (bits 0x%x)", err);
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_morton_codes(const float* points, int64_t n, int dim, const float* lo, const float* hi, int bits,
+                                  uint64_t* codes_out, dbscan_stream stream)
+{
+    t_err.clear();
+    if (n < 0 || (dim != 2 && dim != 3)) return set_error(DBSCAN_ERR_INVALID_ARG, "bad n or dim");
+    if (bits < 1 || dim * bits > 64) return set_error(DBSCAN_ERR_INVALID_ARG, "need 1 <= bits and dim*bits <= 64");
+    if (n > 0 && (!points || !codes_out || !lo || !hi)) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
+    if (n == 0) return DBSCAN_OK;
+    GridParams g{};
+    const float cells = std::ldexp(1.0f, bits);
+    for (int k = 0; k < dim; ++k) {
+        g.lo[k] = lo[k];
+        const float ext = hi[k] - lo[k];
+        g.scale[k] = ext > 0.0f ? cells / ext : 0.0f;
+        g.cmax[k] = (uint32_t)(std::ldexp(1.0, bits) - 1.0);
+    }
+    g.bits = bits;
+    launch_morton_generic(points, n, dim, g, codes_out, static_cast<cudaStream_t>(stream));
+    TRY_CUDA(cudaGetLastError());
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_lbvh_topology(const uint64_t* leaf_keys, int64_t m, int32_t* children_out, int32_t* range_out,
+                                   dbscan_stream stream)
+{
+    t_err.clear();
+    if (m < 2 || m >= (int64_t(1) << 30)) return set_error(DBSCAN_ERR_INVALID_ARG, "need 2 <= m < 2^30");
+    if (!leaf_keys || !children_out || !range_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    Carver c(nullptr);
+    c.take<int4>(m); c.take<int32_t>(2 * m);
+    TRY_CUDA(ensure_arena(w->aux, c.off + 256, s));
+    Carver d(w->aux.base);
+    int4* nmeta = d.take<int4>(m);
+    int32_t* parent = d.take<int32_t>(2 * m);
+    launch_karras_only(leaf_keys, m, nmeta, parent, reinterpret_cast<int2*>(children_out),
+                       reinterpret_cast<int2*>(range_out), s);
+    TRY_CUDA(cudaGetLastError());
+    return DBSCAN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Host-side internals of the C ABI shared by capi.cu, batch.cu and server.cpp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gbdbscan.h"
+
+namespace gbd {
+
+struct Arena {
+    void* base = nullptr;
+    size_t cap = 0;
+};
+
+// One per (device, stream): the pipeline's buffers live in `main`; `aux`
+// serves the component entry points and `io` the host-buffer entry point.
+struct ProfState;
+
+struct Workspace {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Arena main, aux, io;
+    uint32_t* ctrl_host = nullptr;  // pinned mirror of the control block
+    ProfState* prof = nullptr;      // per-stage event records (profiling on)
+};
+
+struct Tuning {
+    int block;          // traversal block size (threads)
+    float cell_factor;  // DenseBox cell side factor f in (0, 1]
+};
+extern Tuning g_tuning;
+
+dbscan_status set_error(dbscan_status st, const char* fmt, ...);
+dbscan_status cuda_error(cudaError_t e, const char* what);
+dbscan_status check_run_args(const void* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
+                             const void* labels_out);
+Workspace* get_workspace(cudaStream_t s);
+cudaError_t ensure_arena(Arena& a, size_t bytes, cudaStream_t s);
+void free_workspace(Workspace* w);
+void release_stream_workspace(cudaStream_t s);
+size_t workspace_bytes(int64_t n, int dim, int algo);
+dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                           int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+
+}  // namespace gbd

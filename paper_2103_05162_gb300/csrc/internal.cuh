@@ -1,0 +1,305 @@
+// Internal declarations shared by the CUDA translation units of libgbdbscan.
+// Nothing here is part of the public C ABI (see include/gbdbscan.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbdbscan.h"
+
+namespace gbd {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int TILE = 32;  // points per non-dense BVH leaf (one warp lane per point)
+
+// bits of the device error word
+constexpr unsigned ERR_SORT_TIMEOUT = 1u;
+
+// Upper bound on the iterations of any device-side wait. A wait that runs out
+// sets an error bit and proceeds, so no kernel can hang.
+constexpr int SPIN_LIMIT = 1 << 22;
+
+// ---------------------------------------------------------------------------
+// The distance test, fixed as the fp32 squared form with no fused multiply-add
+// (explicit round-to-nearest intrinsics, which the compiler never contracts):
+//   dk = fl(x_k - y_k); s = fl(d0*d0); s = fl(s + fl(dk*dk)); adjacent <=> s <= fl(eps*eps)
+// dist(x, y) <= eps is the paper's test (Sec. 2.1); the rounding is this
+// library's fixed reading of it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sqr_rn(float a) { return __fmul_rn(a, a); }
+
+__device__ __forceinline__ float dist2(const float4& a, const float4& b)
+{
+    float s = sqr_rn(__fsub_rn(a.x, b.x));
+    s = __fadd_rn(s, sqr_rn(__fsub_rn(a.y, b.y)));
+    s = __fadd_rn(s, sqr_rn(__fsub_rn(a.z, b.z)));
+    return s;
+}
+
+__device__ __forceinline__ float dist2(const float2& a, const float2& b)
+{
+    float s = sqr_rn(__fsub_rn(a.x, b.x));
+    s = __fadd_rn(s, sqr_rn(__fsub_rn(a.y, b.y)));
+    return s;
+}
+
+// Gap between a coordinate p and the interval [lo, hi]: max(lo - p, p - hi, 0),
+// each difference rounded. Rounding is monotone, so for every y in [lo, hi]
+// |fl(p - y)| >= gap, and the squared box distance below is a lower bound of
+// dist2(p, y) for every point y of the box: pruning with it is exact.
+__device__ __forceinline__ float gap_rn(float lo, float hi, float p)
+{
+    return fmaxf(fmaxf(__fsub_rn(lo, p), __fsub_rn(p, hi)), 0.0f);
+}
+
+// Gap between intervals [alo, ahi] and [blo, bhi] (a lower bound of |a - b|
+// after rounding, for a in A and b in B).
+__device__ __forceinline__ float gap2_rn(float alo, float ahi, float blo, float bhi)
+{
+    return fmaxf(fmaxf(__fsub_rn(blo, ahi), __fsub_rn(alo, bhi)), 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Per-dimension storage traits.
+//   Point: sorted coordinates (float4 with w unused in 3D, float2 in 2D).
+//   Box:   an axis-aligned box, 3D (lo.xyz in a, hi.xyz in b) / 2D (lo.xy, hi.xy in a).
+//   Node:  an internal BVH node holding both children's boxes, their indices,
+//          the split (last leaf of the left child) and the last leaf it covers.
+// ---------------------------------------------------------------------------
+template <int D> struct Traits;
+
+template <> struct Traits<3> {
+    using Point = float4;
+    struct Box { float4 lo, hi; };
+    struct Node { float4 a, b, c; int4 m; };  // 64 B
+
+    __device__ static __forceinline__ Point load_point(const float* p, int64_t i)
+    {
+        return make_float4(p[3 * i], p[3 * i + 1], p[3 * i + 2], 0.0f);
+    }
+    __device__ static __forceinline__ float coord(const Point& p, int k) { return k == 0 ? p.x : (k == 1 ? p.y : p.z); }
+    __device__ static __forceinline__ Box point_box(const Point& p) { return Box{p, p}; }
+    __device__ static __forceinline__ Box empty_box()
+    {
+        return Box{make_float4(INFINITY, INFINITY, INFINITY, 0.f), make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f)};
+    }
+    __device__ static __forceinline__ void grow(Box& b, const Point& p)
+    {
+        b.lo.x = fminf(b.lo.x, p.x); b.lo.y = fminf(b.lo.y, p.y); b.lo.z = fminf(b.lo.z, p.z);
+        b.hi.x = fmaxf(b.hi.x, p.x); b.hi.y = fmaxf(b.hi.y, p.y); b.hi.z = fmaxf(b.hi.z, p.z);
+    }
+    __device__ static __forceinline__ void merge(Box& b, const Box& o)
+    {
+        b.lo.x = fminf(b.lo.x, o.lo.x); b.lo.y = fminf(b.lo.y, o.lo.y); b.lo.z = fminf(b.lo.z, o.lo.z);
+        b.hi.x = fmaxf(b.hi.x, o.hi.x); b.hi.y = fmaxf(b.hi.y, o.hi.y); b.hi.z = fmaxf(b.hi.z, o.hi.z);
+    }
+    __device__ static __forceinline__ Box shfl_xor(const Box& b, int m)
+    {
+        Box r;
+        r.lo.x = __shfl_xor_sync(FULL, b.lo.x, m); r.lo.y = __shfl_xor_sync(FULL, b.lo.y, m);
+        r.lo.z = __shfl_xor_sync(FULL, b.lo.z, m); r.hi.x = __shfl_xor_sync(FULL, b.hi.x, m);
+        r.hi.y = __shfl_xor_sync(FULL, b.hi.y, m); r.hi.z = __shfl_xor_sync(FULL, b.hi.z, m);
+        return r;
+    }
+    // squared distance from p to box (lower bound of dist2 to any point inside)
+    __device__ static __forceinline__ float box_dist2(const Point& p, float lx, float ly, float lz, float hx, float hy, float hz)
+    {
+        float s = sqr_rn(gap_rn(lx, hx, p.x));
+        s = __fadd_rn(s, sqr_rn(gap_rn(ly, hy, p.y)));
+        s = __fadd_rn(s, sqr_rn(gap_rn(lz, hz, p.z)));
+        return s;
+    }
+    __device__ static __forceinline__ float box_box_dist2(const Box& a, float lx, float ly, float lz, float hx, float hy, float hz)
+    {
+        float s = sqr_rn(gap2_rn(a.lo.x, a.hi.x, lx, hx));
+        s = __fadd_rn(s, sqr_rn(gap2_rn(a.lo.y, a.hi.y, ly, hy)));
+        s = __fadd_rn(s, sqr_rn(gap2_rn(a.lo.z, a.hi.z, lz, hz)));
+        return s;
+    }
+    // diameter test of a box: the squared distance of its corners
+    __device__ static __forceinline__ float diag2(const Box& b) { return dist2(b.lo, b.hi); }
+    __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
+    {
+        Node n;
+        n.a = make_float4(L.lo.x, L.lo.y, L.lo.z, L.hi.x);
+        n.b = make_float4(L.hi.y, L.hi.z, R.lo.x, R.lo.y);
+        n.c = make_float4(R.lo.z, R.hi.x, R.hi.y, R.hi.z);
+        n.m = make_int4(left, right, split, last);
+        return n;
+    }
+};
+
+template <> struct Traits<2> {
+    using Point = float2;
+    struct Box { float4 lo, hi; };  // z unused
+    struct Node { float4 a, b; int4 m; };  // 48 B
+
+    __device__ static __forceinline__ Point load_point(const float* p, int64_t i)
+    {
+        return make_float2(p[2 * i], p[2 * i + 1]);
+    }
+    __device__ static __forceinline__ float coord(const Point& p, int k) { return k == 0 ? p.x : p.y; }
+    __device__ static __forceinline__ Box point_box(const Point& p)
+    {
+        return Box{make_float4(p.x, p.y, 0.f, 0.f), make_float4(p.x, p.y, 0.f, 0.f)};
+    }
+    __device__ static __forceinline__ Box empty_box()
+    {
+        return Box{make_float4(INFINITY, INFINITY, 0.f, 0.f), make_float4(-INFINITY, -INFINITY, 0.f, 0.f)};
+    }
+    __device__ static __forceinline__ void grow(Box& b, const Point& p)
+    {
+        b.lo.x = fminf(b.lo.x, p.x); b.lo.y = fminf(b.lo.y, p.y);
+        b.hi.x = fmaxf(b.hi.x, p.x); b.hi.y = fmaxf(b.hi.y, p.y);
+    }
+    __device__ static __forceinline__ void merge(Box& b, const Box& o)
+    {
+        b.lo.x = fminf(b.lo.x, o.lo.x); b.lo.y = fminf(b.lo.y, o.lo.y);
+        b.hi.x = fmaxf(b.hi.x, o.hi.x); b.hi.y = fmaxf(b.hi.y, o.hi.y);
+    }
+    __device__ static __forceinline__ Box shfl_xor(const Box& b, int m)
+    {
+        Box r = b;
+        r.lo.x = __shfl_xor_sync(FULL, b.lo.x, m); r.lo.y = __shfl_xor_sync(FULL, b.lo.y, m);
+        r.hi.x = __shfl_xor_sync(FULL, b.hi.x, m); r.hi.y = __shfl_xor_sync(FULL, b.hi.y, m);
+        return r;
+    }
+    __device__ static __forceinline__ float box_dist2(const Point& p, float lx, float ly, float hx, float hy)
+    {
+        float s = sqr_rn(gap_rn(lx, hx, p.x));
+        s = __fadd_rn(s, sqr_rn(gap_rn(ly, hy, p.y)));
+        return s;
+    }
+    __device__ static __forceinline__ float box_box_dist2(const Box& a, float lx, float ly, float hx, float hy)
+    {
+        float s = sqr_rn(gap2_rn(a.lo.x, a.hi.x, lx, hx));
+        s = __fadd_rn(s, sqr_rn(gap2_rn(a.lo.y, a.hi.y, ly, hy)));
+        return s;
+    }
+    __device__ static __forceinline__ float diag2(const Box& b)
+    {
+        return dist2(make_float2(b.lo.x, b.lo.y), make_float2(b.hi.x, b.hi.y));
+    }
+    __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
+    {
+        Node n;
+        n.a = make_float4(L.lo.x, L.lo.y, L.hi.x, L.hi.y);
+        n.b = make_float4(R.lo.x, R.lo.y, R.hi.x, R.hi.y);
+        n.m = make_int4(left, right, split, last);
+        return n;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Synchronisation-free union-find over a flat labels array (Sec. 4.3): the
+// label of a point is its parent; a root is its own label. Unions hook the
+// larger root under the smaller with one compare-and-swap, so every root is
+// the smallest (sorted) index of its set. find() halves the path as it goes
+// ("intermediate pointer jumping"): each visited element is pointed at its
+// grandparent, which is always an ancestor, so concurrent finds stay correct.
+// Reads bypass L1 (labels change under the feet of other SMs).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int uf_find(int* L, int x)
+{
+    int p = __ldcg(L + x);
+    while (p != x) {
+        int gp = __ldcg(L + p);
+        if (gp == p) return p;
+        __stcg(L + x, gp);
+        x = gp;
+        p = __ldcg(L + x);
+    }
+    return x;
+}
+
+// find without writes (for read-only passes once the forest is final)
+__device__ __forceinline__ int uf_root(const int* L, int x)
+{
+    int p = __ldcg(L + x);
+    while (p != x) { x = p; p = __ldcg(L + x); }
+    return x;
+}
+
+__device__ __forceinline__ void uf_union(int* L, int a, int b)
+{
+    for (;;) {
+        a = uf_find(L, a);
+        b = uf_find(L, b);
+        if (a == b) return;
+        if (a > b) { int t = a; a = b; b = t; }
+        int old = atomicCAS(L + b, b, a);
+        if (old == b) return;
+    }
+}
+
+// A non-core point y joins the cluster of core point x if it has not joined
+// one yet (labels[y] == y). The compare-and-swap replaces the critical
+// section of Algorithm 3 (Sec. 3.2): y is never a union target, so a border
+// point cannot bridge two clusters.
+__device__ __forceinline__ void uf_claim(int* L, int y, int x)
+{
+    if (__ldcg(L + y) != y) return;
+    int r = uf_find(L, x);
+    atomicCAS(L + y, y, r);
+}
+
+// relaxed global loads/stores for look-back status words
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// float <-> order-preserving uint (for atomic min/max of floats)
+__device__ __forceinline__ uint32_t f2ord(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float ord2f(uint32_t u)
+{
+    uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+// Count of kernels this library has launched (for the benchmark's claim of
+// how many of its kernels ran); every launcher adds what it launches.
+void note_launches(int k);
+int64_t launches_so_far();
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files).
+// ---------------------------------------------------------------------------
+
+// sort.cu
+struct SortBuffers {
+    void* keys_alt;        // n keys
+    uint32_t* vals_alt;    // n values
+    uint32_t* hist;        // 8 * 256
+    uint32_t* status;      // passes * tiles * 256
+    uint32_t* counters;    // 8
+    uint32_t* err;         // device error word
+};
+int64_t sort_tiles(int64_t n, int key_bytes);
+size_t sort_status_words(int64_t n, int key_bytes, int bits);
+// Sorts (keys, vals) by the low `bits` bits. On return *in_alt tells whether
+// the sorted data ended in the alternate buffers.
+cudaError_t sort_pairs_u32(uint32_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
+                           cudaStream_t s, bool* in_alt);
+cudaError_t sort_pairs_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
+                           cudaStream_t s, bool* in_alt);
+
+// scan.cu: out[i] = op(in[0..i]) (inclusive) or op(in[0..i-1]) (exclusive, out[0] = identity)
+enum ScanOp { SCAN_ADD = 0, SCAN_MAX = 1 };
+size_t scan_temp_words(int64_t n);
+cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t n, ScanOp op, bool inclusive, int32_t* temp,
+                     cudaStream_t s);
+
+}  // namespace gbd

@@ -1,0 +1,262 @@
+// Stable LSD radix sort of (key, value) pairs, onesweep style: one kernel
+// builds the digit histograms of every pass in a single read of the keys;
+// then each 8-bit pass is a single kernel in which a tile ranks its keys in
+// shared memory, publishes its per-digit counts, finds its global offsets by
+// decoupled look-back over the tiles before it, and scatters.
+//
+// Forward progress: tiles take their index from an atomic counter when they
+// start, so a tile only ever waits for tiles that are already running. Every
+// wait is bounded (SPIN_LIMIT); a wait that runs out sets ERR_SORT_TIMEOUT in
+// the device error word instead of hanging.
+//
+// This orders Morton codes / grid-cell keys (the space-filling-curve order of
+// Sec. 4.1 and the cell grouping of Sec. 4.2).
+#include "internal.cuh"
+
+namespace gbd {
+
+namespace {
+
+constexpr int THREADS = 256;  // == radix: thread t owns digit t in the per-digit steps
+constexpr int WARPS = THREADS / 32;
+constexpr int RADIX = 256;
+constexpr int ITEMS = 16;
+constexpr int TILE_ITEMS = THREADS * ITEMS;
+constexpr uint32_t FLAG_AGG = 1u << 30;
+constexpr uint32_t FLAG_PRE = 2u << 30;
+constexpr uint32_t VAL_MASK = (1u << 30) - 1;
+
+template <typename K>
+__global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, int64_t n, int passes,
+                                                  uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t sh[8 * RADIX];
+    for (int i = threadIdx.x; i < passes * RADIX; i += THREADS) sh[i] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS) {
+        K k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (8 * p)) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RADIX; i += THREADS) {
+        uint32_t v = sh[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// exclusive scan of one value per thread over the 256 threads of the block
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < WARPS ? s_warp[lane] : 0;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < WARPS) s_warp[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t r = inc - x + s_warp[warp];
+    __syncthreads();
+    return r;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(THREADS) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, const uint32_t* __restrict__ hist,
+                                                      uint32_t* __restrict__ status, uint32_t* tile_counter,
+                                                      uint32_t* err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    K* keys_s = reinterpret_cast<K*>(smem);
+    uint32_t* vals_s = reinterpret_cast<uint32_t*>(smem + TILE_ITEMS * sizeof(K));
+    uint32_t* whist = reinterpret_cast<uint32_t*>(smem);  // [WARPS][RADIX], aliases keys_s
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_excl[RADIX];
+    __shared__ uint32_t s_gofs[RADIX];
+    __shared__ uint32_t s_warp[WARPS];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    for (int i = tid; i < WARPS * RADIX; i += THREADS) whist[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * TILE_ITEMS;
+    const int64_t wbase = base + warp * (32 * ITEMS);
+
+    K k[ITEMS];
+    uint32_t v[ITEMS];
+    uint32_t r[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int64_t idx = wbase + i * 32 + lane;
+        if (idx < n) {
+            k[i] = kin[idx];
+            v[i] = vin[idx];
+        } else {
+            k[i] = ~K(0);
+            v[i] = 0;
+        }
+    }
+    // rank each key among equal digits of its warp, in input order
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const bool valid = (wbase + i * 32 + lane) < n;
+        const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+        uint32_t peers = __ballot_sync(FULL, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t bit = (d >> b) & 1u;
+            const uint32_t m = __ballot_sync(FULL, bit);
+            peers &= bit ? m : ~m;
+        }
+        uint32_t* h = &whist[warp * RADIX + d];
+        const uint32_t prior = valid ? *h : 0u;
+        __syncwarp();
+        if (valid && lane == 31 - __clz(peers)) *h = prior + __popc(peers);
+        __syncwarp();
+        r[i] = prior + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // thread tid owns digit tid: per-warp exclusive offsets and the tile count
+    uint32_t total = 0;
+    for (int w = 0; w < WARPS; ++w) {
+        uint32_t c = whist[w * RADIX + tid];
+        whist[w * RADIX + tid] = total;
+        total += c;
+    }
+    uint32_t* st = status + (size_t)tile * RADIX + tid;
+    st_relaxed(st, (tile == 0 ? FLAG_PRE : FLAG_AGG) | total);
+
+    const uint32_t excl = block_excl_scan(total, s_warp);
+    s_excl[tid] = excl;
+    const uint32_t dbase = block_excl_scan(hist[tid], s_warp);
+
+    uint32_t prefix = 0;
+    if (tile > 0) {
+        int64_t j = (int64_t)tile - 1;
+        int spins = 0;
+        while (j >= 0) {
+            const uint32_t s = ld_relaxed(status + (size_t)j * RADIX + tid);
+            const uint32_t flag = s & ~VAL_MASK;
+            if (flag == 0u) {
+                if (++spins > SPIN_LIMIT) {
+                    atomicOr(err, ERR_SORT_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            prefix += s & VAL_MASK;
+            if (flag == FLAG_PRE) break;
+            --j;
+        }
+        st_relaxed(st, FLAG_PRE | ((prefix + total) & VAL_MASK));
+    }
+    s_gofs[tid] = dbase + prefix;
+    __syncthreads();
+
+    // tile-local positions (sorted by digit, stable), then stage in shared memory
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+        r[i] += s_excl[d] + whist[warp * RADIX + d];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if ((wbase + i * 32 + lane) < n) {
+            keys_s[r[i]] = k[i];
+            vals_s[r[i]] = v[i];
+        }
+    }
+    __syncthreads();
+    const int64_t rem = n - base;
+    const int cnt = rem < TILE_ITEMS ? (int)rem : TILE_ITEMS;
+    for (int j = tid; j < cnt; j += THREADS) {
+        const K kk = keys_s[j];
+        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        const uint32_t o = s_gofs[d] + (uint32_t)j - s_excl[d];
+        kout[o] = kk;
+        vout[o] = vals_s[j];
+    }
+}
+
+template <typename K>
+cudaError_t sort_pairs(K* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb, cudaStream_t s,
+                       bool* in_alt)
+{
+    *in_alt = false;
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    const int passes = (bits + 7) / 8;
+    const int64_t tiles = (n + TILE_ITEMS - 1) / TILE_ITEMS;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(sb.hist, 0, sizeof(uint32_t) * RADIX * passes, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sb.counters, 0, sizeof(uint32_t) * passes, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sb.status, 0, sizeof(uint32_t) * RADIX * (size_t)tiles * passes, s)) != cudaSuccess)
+        return e;
+    const int hist_blocks = (int)(tiles < 1216 ? tiles : 1216);
+    k_hist<K><<<hist_blocks, THREADS, 0, s>>>(keys, n, passes, sb.hist);
+    note_launches(1);
+    const size_t smem = TILE_ITEMS * (sizeof(K) + sizeof(uint32_t));
+    static_assert(TILE_ITEMS * sizeof(uint32_t) >= WARPS * RADIX * sizeof(uint32_t), "histograms alias keys");
+    if ((e = cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    K* kin = keys;
+    uint32_t* vin = vals;
+    K* kout = static_cast<K*>(sb.keys_alt);
+    uint32_t* vout = sb.vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        k_onesweep<K><<<(unsigned)tiles, THREADS, smem, s>>>(kin, vin, kout, vout, n, 8 * p, sb.hist + RADIX * p,
+                                                              sb.status + (size_t)RADIX * tiles * p,
+                                                              sb.counters + p, sb.err);
+        note_launches(1);
+        K* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    *in_alt = (passes & 1) != 0;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t sort_tiles(int64_t n, int key_bytes)
+{
+    (void)key_bytes;
+    return (n + TILE_ITEMS - 1) / TILE_ITEMS;
+}
+
+size_t sort_status_words(int64_t n, int key_bytes, int bits)
+{
+    const int passes = (bits + 7) / 8;
+    return (size_t)RADIX * (size_t)sort_tiles(n, key_bytes) * (size_t)(passes > 0 ? passes : 1);
+}
+
+cudaError_t sort_pairs_u32(uint32_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
+                           cudaStream_t s, bool* in_alt)
+{
+    return sort_pairs<uint32_t>(keys, vals, n, bits, sb, s, in_alt);
+}
+
+cudaError_t sort_pairs_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
+                           cudaStream_t s, bool* in_alt)
+{
+    return sort_pairs<uint64_t>(keys, vals, n, bits, sb, s, in_alt);
+}
+
+}  // namespace gbd

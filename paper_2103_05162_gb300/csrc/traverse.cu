@@ -1,0 +1,640 @@
+// The two traversal phases of the parallel disjoint-set DBSCAN (Sec. 3.2,
+// Algorithm 3) over the BVH of Sec. 4.1/4.2, plus union-find initialisation,
+// final compression (Sec. 4.3) and canonical relabelling.
+//
+// Work is organised per BVH leaf and per warp: a leaf is either a tile of up
+// to 32 consecutive sorted points outside dense cells (one point per lane) or
+// a whole dense cell (Sec. 4.2). A warp takes the next leaf from a global
+// counter (persistent kernels), and its 32 lanes traverse the tree together
+// with one shared stack: at each node every lane tests its own point against
+// both children's boxes (stored in the node record) and the warp descends
+// where any lane hits. At a leaf, pairs are tested either lane-per-query
+// (looping over the leaf's points) or lane-per-leaf-point (looping over the
+// queries that reached the leaf), whichever needs fewer steps.
+//
+// Preprocessing (minPts > 2 only): each point outside dense cells counts its
+// neighbours (itself included) and stops at minPts; points of dense cells are
+// core by construction.
+// Main: each leaf visits only the leaves with index >= its own (the pair mask
+// of Sec. 4.1, Figure "pair traversal"), so every pair is seen once, and
+// applies the rule of Algorithm 3 as it finds each pair, with no neighbour
+// list: core-core pairs are united, a core point claims a non-core neighbour
+// with one compare-and-swap (Sec. 3.2). A dense cell needs only one adjacent
+// point to be found (Sec. 4.2).
+#include "build.cuh"
+
+namespace gbd {
+
+namespace {
+
+constexpr int STACK = 128;  // > the largest possible tree depth (97 for 64-bit keys + index tie-break)
+
+template <int D> struct NB;
+template <> struct NB<3> {
+    using T = Traits<3>;
+    __device__ static __forceinline__ T::Node load(const T::Node* n, int i)
+    {
+        T::Node r;
+        r.a = __ldg(&n[i].a); r.b = __ldg(&n[i].b); r.c = __ldg(&n[i].c); r.m = __ldg(&n[i].m);
+        return r;
+    }
+    __device__ static __forceinline__ float pl(const T::Node& n, const T::Point& p)
+    {
+        return T::box_dist2(p, n.a.x, n.a.y, n.a.z, n.a.w, n.b.x, n.b.y);
+    }
+    __device__ static __forceinline__ float pr(const T::Node& n, const T::Point& p)
+    {
+        return T::box_dist2(p, n.b.z, n.b.w, n.c.x, n.c.y, n.c.z, n.c.w);
+    }
+    __device__ static __forceinline__ float bl(const T::Node& n, const T::Box& q)
+    {
+        return T::box_box_dist2(q, n.a.x, n.a.y, n.a.z, n.a.w, n.b.x, n.b.y);
+    }
+    __device__ static __forceinline__ float br(const T::Node& n, const T::Box& q)
+    {
+        return T::box_box_dist2(q, n.b.z, n.b.w, n.c.x, n.c.y, n.c.z, n.c.w);
+    }
+    __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
+    {
+        return make_float4(__shfl_sync(FULL, p.x, src), __shfl_sync(FULL, p.y, src), __shfl_sync(FULL, p.z, src), 0.f);
+    }
+};
+template <> struct NB<2> {
+    using T = Traits<2>;
+    __device__ static __forceinline__ T::Node load(const T::Node* n, int i)
+    {
+        T::Node r;
+        r.a = __ldg(&n[i].a); r.b = __ldg(&n[i].b); r.m = __ldg(&n[i].m);
+        return r;
+    }
+    __device__ static __forceinline__ float pl(const T::Node& n, const T::Point& p)
+    {
+        return T::box_dist2(p, n.a.x, n.a.y, n.a.z, n.a.w);
+    }
+    __device__ static __forceinline__ float pr(const T::Node& n, const T::Point& p)
+    {
+        return T::box_dist2(p, n.b.x, n.b.y, n.b.z, n.b.w);
+    }
+    __device__ static __forceinline__ float bl(const T::Node& n, const T::Box& q)
+    {
+        return T::box_box_dist2(q, n.a.x, n.a.y, n.a.z, n.a.w);
+    }
+    __device__ static __forceinline__ float br(const T::Node& n, const T::Box& q)
+    {
+        return T::box_box_dist2(q, n.b.x, n.b.y, n.b.z, n.b.w);
+    }
+    __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
+    {
+        return make_float2(__shfl_sync(FULL, p.x, src), __shfl_sync(FULL, p.y, src));
+    }
+};
+
+template <int D>
+struct WarpMem {
+    typename Traits<D>::Point buf[32];
+    int stack[STACK];
+    uint8_t cbuf[32];
+};
+
+// Warp-cooperative stack traversal. Children whose last leaf is below
+// v.mask_lo are never entered (the pair mask). Returns when the stack is
+// empty or when v.leaf() asks to stop (early termination).
+template <int D, class V>
+__device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes, int64_t m, V& v,
+                                         int* stack, uint32_t* ctrl)
+{
+    const int lane = threadIdx.x & 31;
+    if (m == 1) {
+        v.leaf(0, v.root_mask());
+        return;
+    }
+    const int leaf0 = (int)(m - 1);
+    int node = 0, sp = 0;
+    // a traversal enters each internal node at most once; more steps than
+    // that can only come from a corrupt tree: flag it and stop
+    int64_t steps = 0;
+    for (;;) {
+        if (++steps > m) {
+            if (lane == 0) atomicOr(&ctrl[CTRL_ERR], ERR_STACK);
+            return;
+        }
+        const auto nd = NB<D>::load(nodes, node);
+        unsigned ml = 0, mr = 0;
+        if (nd.m.z >= v.mask_lo) ml = __ballot_sync(FULL, v.hit_l(nd));
+        if (nd.m.w >= v.mask_lo) mr = __ballot_sync(FULL, v.hit_r(nd));
+        int next = -1;
+        if (ml) {
+            if (nd.m.x >= leaf0) {
+                if (v.leaf(nd.m.x - leaf0, ml)) return;
+            } else {
+                next = nd.m.x;
+            }
+        }
+        if (mr) {
+            if (nd.m.y >= leaf0) {
+                if (v.leaf(nd.m.y - leaf0, mr)) return;
+            } else if (next < 0) {
+                next = nd.m.y;
+            } else {
+                if (sp >= STACK) {
+                    if (lane == 0) atomicOr(&ctrl[CTRL_ERR], ERR_STACK);
+                    return;
+                }
+                if (lane == 0) stack[sp] = nd.m.y;
+                ++sp;
+            }
+        }
+        if (next < 0) {
+            if (sp == 0) return;
+            __syncwarp();
+            next = stack[--sp];
+        }
+        node = next;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preprocessing visitor: count neighbours up to minPts (Sec. 3.2, 4.1, 4.2).
+// ---------------------------------------------------------------------------
+template <int D>
+struct PreV {
+    using T = Traits<D>;
+    using P = typename T::Point;
+    const P* __restrict__ sp;
+    const int2* __restrict__ leafr;
+    P* buf;
+    float e2;
+    int min_pts;
+    int mask_lo;
+    int lane;
+    P p;
+    bool act;
+    int cnt;
+
+    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return act && NB<D>::pl(n, p) <= e2; }
+    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return act && NB<D>::pr(n, p) <= e2; }
+    __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, act); }
+
+    __device__ bool leaf(int L, unsigned mask)
+    {
+        const int2 r = __ldg(&leafr[L]);
+        const int s = r.x, e = r.y & 0x7fffffff;
+        mask &= __ballot_sync(FULL, act);
+        for (int c = s; c < e && mask; c += 32) {
+            const int k = min(32, e - c);
+            if (__popc(mask) < k) {
+                // lane per leaf point, looping over the queries in `mask`
+                const bool in = lane < k;
+                const P rp = in ? sp[c + lane] : sp[c];
+                unsigned mm = mask;
+                while (mm) {
+                    const int q = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const P pq = NB<D>::shfl(p, q);
+                    const unsigned h = __ballot_sync(FULL, in && dist2(pq, rp) <= e2);
+                    if (lane == q) {
+                        cnt += __popc(h);
+                        if (cnt >= min_pts) act = false;
+                    }
+                }
+            } else {
+                // lane per query, looping over the staged leaf points
+                if (lane < k) buf[lane] = sp[c + lane];
+                __syncwarp();
+                if ((mask >> lane) & 1u) {
+                    for (int u = 0; u < k; ++u) {
+                        if (dist2(p, buf[u]) <= e2 && ++cnt >= min_pts) {
+                            act = false;
+                            break;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            mask &= __ballot_sync(FULL, act);
+        }
+        return !__any_sync(FULL, act);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The pair rule of Algorithm 3 (Sec. 3.2), for a pair (a, b) within eps.
+// ---------------------------------------------------------------------------
+struct Rule {
+    int* labels;
+    uint8_t* core;
+    int min_pts;
+    int mode;
+
+    __device__ __forceinline__ void unite(int a, int b) const
+    {
+        if (__ldcg(labels + a) == __ldcg(labels + b)) return;  // same parent: same set
+        uf_union(labels, a, b);
+    }
+    __device__ __forceinline__ void pair(int a, bool acore, int b, bool bcore) const
+    {
+        if (min_pts <= 2) {
+            // no preprocessing: any pair makes both points core (Sec. 3.2)
+            if (min_pts == 2) { core[a] = 1; core[b] = 1; }
+            unite(a, b);
+        } else if (acore && bcore) {
+            unite(a, b);
+        } else if (mode == DBSCAN_MODE_DBSCAN) {
+            if (acore) uf_claim(labels, b, a);
+            else if (bcore) uf_claim(labels, a, b);
+        }
+    }
+    // would point x (core flag xcore) change anything by joining the dense
+    // cell whose first point is s?
+    __device__ __forceinline__ bool need_dense(int x, bool xcore, int s) const
+    {
+        if (min_pts <= 2 || xcore) return uf_find(labels, x) != uf_find(labels, s);
+        return mode == DBSCAN_MODE_DBSCAN && __ldcg(labels + x) == x;
+    }
+    __device__ __forceinline__ void join_dense(int x, bool xcore, int s) const
+    {
+        if (min_pts <= 2 || xcore) {
+            if (min_pts == 2) core[x] = 1;
+            uf_union(labels, x, s);
+        } else {
+            uf_claim(labels, x, s);
+        }
+    }
+};
+
+// Main visitor for a tile of points outside dense cells (one point per lane).
+template <int D>
+struct MainPtV {
+    using T = Traits<D>;
+    using P = typename T::Point;
+    const P* __restrict__ sp;
+    const int2* __restrict__ leafr;
+    const uint8_t* core;
+    P* buf;
+    uint8_t* cbuf;
+    Rule rule;
+    float e2;
+    int mask_lo;  // = own leaf index
+    int lane;
+    int sQ;       // first point of own leaf
+    P p;
+    int q;
+    bool valid;
+    bool qcore;
+
+    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return valid && NB<D>::pl(n, p) <= e2; }
+    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return valid && NB<D>::pr(n, p) <= e2; }
+    __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
+
+    __device__ bool leaf(int L, unsigned mask)
+    {
+        const int2 r = __ldg(&leafr[L]);
+        const int s = r.x, e = r.y & 0x7fffffff;
+        const bool dense = r.y < 0;
+        if (L == mask_lo) {
+            // own tile: the pairs (q, q') with q' > q
+            const int k = e - s;
+            if (lane < k) { buf[lane] = p; cbuf[lane] = qcore ? 1 : 0; }
+            __syncwarp();
+            if (valid)
+                for (int u = lane + 1; u < k; ++u)
+                    if (dist2(p, buf[u]) <= e2) rule.pair(q, qcore, s + u, cbuf[u] != 0);
+            __syncwarp();
+            return false;
+        }
+        if (!dense) {
+            const int k = e - s;
+            if (__popc(mask) < k) {
+                const bool in = lane < k;
+                const int ri = s + lane;
+                const P rp = in ? sp[ri] : sp[s];
+                const bool rc = in && core[ri];
+                unsigned mm = mask;
+                while (mm) {
+                    const int qq = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const P pq = NB<D>::shfl(p, qq);
+                    const bool qc = __shfl_sync(FULL, qcore, qq);
+                    if (in && dist2(pq, rp) <= e2) rule.pair(sQ + qq, qc, ri, rc);
+                    __syncwarp();
+                }
+            } else {
+                if (lane < k) { buf[lane] = sp[s + lane]; cbuf[lane] = core[s + lane]; }
+                __syncwarp();
+                if ((mask >> lane) & 1u)
+                    for (int u = 0; u < k; ++u)
+                        if (dist2(p, buf[u]) <= e2) rule.pair(q, qcore, s + u, cbuf[u] != 0);
+                __syncwarp();
+            }
+            return false;
+        }
+        // dense cell: one adjacent point decides (all its points are core and
+        // already one set rooted at its first point s)
+        const bool need = ((mask >> lane) & 1u) && rule.need_dense(q, qcore, s);
+        unsigned nm = __ballot_sync(FULL, need);
+        while (nm) {
+            const int qq = __ffs(nm) - 1;
+            nm &= nm - 1;
+            const P pq = NB<D>::shfl(p, qq);
+            bool found = false;
+            for (int c = s; c < e; c += 32) {
+                const int j = c + lane;
+                const bool h = j < e && dist2(pq, sp[j]) <= e2;
+                if (__any_sync(FULL, h)) { found = true; break; }
+            }
+            if (found && lane == qq) rule.join_dense(q, qcore, s);
+            __syncwarp();
+        }
+        return false;
+    }
+};
+
+// Main visitor for a dense cell as the query (its box is tested against the
+// nodes; its points are all core and already one set).
+template <int D>
+struct MainBoxV {
+    using T = Traits<D>;
+    using P = typename T::Point;
+    const P* __restrict__ sp;
+    const int2* __restrict__ leafr;
+    const uint8_t* core;
+    P* buf;
+    Rule rule;
+    float e2;
+    int mask_lo;  // = own leaf index
+    int lane;
+    int sQ, eQ;
+    typename T::Box qb;
+
+    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return NB<D>::bl(n, qb) <= e2; }
+    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return NB<D>::br(n, qb) <= e2; }
+    __device__ __forceinline__ unsigned root_mask() const { return FULL; }
+
+    __device__ bool leaf(int L, unsigned)
+    {
+        if (L == mask_lo) return false;
+        const int2 r = __ldg(&leafr[L]);
+        const int s = r.x, e = r.y & 0x7fffffff;
+        const bool dense = r.y < 0;
+        if (dense) {
+            int same = 0;
+            if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
+            if (__shfl_sync(FULL, same, 0)) return false;
+            bool found = false;
+            for (int cq = sQ; cq < eQ && !found; cq += 32) {
+                const int iq = cq + lane;
+                const bool inq = iq < eQ;
+                const P pq = inq ? sp[iq] : sp[sQ];
+                for (int c = s; c < e; c += 32) {
+                    const int k = min(32, e - c);
+                    if (lane < k) buf[lane] = sp[c + lane];
+                    __syncwarp();
+                    bool h = false;
+                    if (inq)
+                        for (int u = 0; u < k; ++u)
+                            if (dist2(pq, buf[u]) <= e2) { h = true; break; }
+                    __syncwarp();
+                    if (__any_sync(FULL, h)) { found = true; break; }
+                }
+            }
+            if (found && lane == 0) uf_union(rule.labels, sQ, s);
+            __syncwarp();
+            return false;
+        }
+        // a tile of points outside dense cells: one lane per point
+        const int k = e - s;
+        const bool in = lane < k;
+        const int ri = s + lane;
+        const P rp = in ? sp[ri] : sp[s];
+        const bool rc = in && core[ri];
+        const bool need = in && rule.need_dense(ri, rc, sQ);
+        bool found = false;
+        for (int cq = sQ; cq < eQ; cq += 32) {
+            if (!__any_sync(FULL, need && !found)) break;
+            const int kq = min(32, eQ - cq);
+            if (lane < kq) buf[lane] = sp[cq + lane];
+            __syncwarp();
+            if (need && !found)
+                for (int u = 0; u < kq; ++u)
+                    if (dist2(rp, buf[u]) <= e2) { found = true; break; }
+            __syncwarp();
+        }
+        if (need && found) rule.join_dense(ri, rc, sQ);
+        __syncwarp();
+        return false;
+    }
+};
+
+template <int D>
+struct DevArgs {
+    const typename Traits<D>::Point* sp;
+    const typename Traits<D>::Node* nodes;
+    const typename Traits<D>::Box* nodebox;
+    const int2* leafr;
+    int32_t* labels;
+    uint8_t* core;
+    uint32_t* ctrl;
+    float e2;
+    int min_pts;
+    int mode;
+};
+
+__device__ __forceinline__ int next_leaf(uint32_t* ctr)
+{
+    int L = 0;
+    if ((threadIdx.x & 31) == 0) L = (int)atomicAdd(ctr, 1u);
+    return __shfl_sync(FULL, L, 0);
+}
+
+template <int D>
+__global__ void k_pre(DevArgs<D> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t m = a.ctrl[CTRL_M];
+    for (;;) {
+        const int L = next_leaf(&a.ctrl[CTRL_WORK_PRE]);
+        if (L >= m) break;
+        const int2 r = a.leafr[L];
+        if (r.y < 0) continue;  // dense cell: all core already
+        const int s = r.x, e = r.y;
+        const int q = s + lane;
+        PreV<D> v;
+        v.sp = a.sp; v.leafr = a.leafr; v.buf = wm->buf; v.e2 = a.e2; v.min_pts = a.min_pts;
+        v.mask_lo = 0; v.lane = lane;
+        v.act = q < e;
+        v.p = a.sp[v.act ? q : s];
+        v.cnt = 0;
+        traverse<D>(a.nodes, m, v, wm->stack, a.ctrl);
+        if (q < e) a.core[q] = v.cnt >= a.min_pts ? 1 : 0;
+    }
+}
+
+template <int D>
+__global__ void k_main(DevArgs<D> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t m = a.ctrl[CTRL_M];
+    Rule rule{a.labels, a.core, a.min_pts, a.mode};
+    for (;;) {
+        const int L = next_leaf(&a.ctrl[CTRL_WORK_MAIN]);
+        if (L >= m) break;
+        const int2 r = a.leafr[L];
+        const int s = r.x, e = r.y & 0x7fffffff;
+        if (r.y >= 0) {
+            MainPtV<D> v;
+            v.sp = a.sp; v.leafr = a.leafr; v.core = a.core; v.buf = wm->buf; v.cbuf = wm->cbuf;
+            v.rule = rule; v.e2 = a.e2; v.mask_lo = L; v.lane = lane; v.sQ = s;
+            v.q = s + lane;
+            v.valid = v.q < e;
+            v.p = a.sp[v.valid ? v.q : s];
+            v.qcore = v.valid && a.core[v.q];
+            traverse<D>(a.nodes, m, v, wm->stack, a.ctrl);
+        } else {
+            MainBoxV<D> v;
+            v.sp = a.sp; v.leafr = a.leafr; v.core = a.core; v.buf = wm->buf;
+            v.rule = rule; v.e2 = a.e2; v.mask_lo = L; v.lane = lane; v.sQ = s; v.eQ = e;
+            v.qb.lo = a.nodebox[(m - 1) + L].lo;
+            v.qb.hi = a.nodebox[(m - 1) + L].hi;
+            traverse<D>(a.nodes, m, v, wm->stack, a.ctrl);
+        }
+    }
+}
+
+// labels[i] = i (or the dense cell's first point); core = 1 in dense cells
+// (and everywhere when minPts == 1)
+__global__ void k_init(const int2* __restrict__ leafr, const uint32_t* __restrict__ ctrl, int min_pts,
+                       int32_t* __restrict__ labels, uint8_t* __restrict__ core)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t m = ctrl[CTRL_M];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = wid; l < m; l += nw) {
+        const int2 r = leafr[l];
+        const int s = r.x, e = r.y & 0x7fffffff;
+        const bool dense = r.y < 0;
+        for (int j = s + lane; j < e; j += 32) {
+            labels[j] = dense ? s : j;
+            core[j] = (dense || min_pts == 1) ? 1 : 0;
+        }
+    }
+}
+
+// full compression (Sec. 4.3) and the smallest input index per root
+__global__ void k_finalize(int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
+                           int64_t n, int32_t* __restrict__ canon)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = uf_find(labels, (int)i);
+        if (core[i]) atomicMin(&canon[r], (int32_t)perm[i]);
+    }
+}
+
+// output in input order: canonical label of the cluster, or -1
+__global__ void k_relabel(const int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
+                          int64_t n, int mode, const int32_t* __restrict__ canon, int32_t* __restrict__ out,
+                          uint8_t* __restrict__ core_out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const bool c = core[i] != 0;
+        const int r = uf_root(labels, (int)i);
+        const bool member = c || (mode == DBSCAN_MODE_DBSCAN && r != (int)i);
+        const uint32_t o = perm[i];
+        out[o] = member ? canon[r] : -1;
+        if (core_out) core_out[o] = c ? 1 : 0;
+    }
+}
+
+template <int D>
+int persistent_blocks(const void* kernel, int block, size_t smem)
+{
+    static int cached[2][33] = {};
+    const int which = kernel == (const void*)k_pre<D> ? 0 : 1;
+    int& c = cached[which][block / 32];
+    if (c == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem);
+        c = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    }
+    return c;
+}
+
+template <int D>
+DevArgs<D> dev_args(const ClusterArgs& a)
+{
+    DevArgs<D> d;
+    d.sp = static_cast<const typename Traits<D>::Point*>(a.sp);
+    d.nodes = static_cast<const typename Traits<D>::Node*>(a.nodes);
+    d.nodebox = static_cast<const typename Traits<D>::Box*>(a.nodebox);
+    d.leafr = a.leafr;
+    d.labels = a.labels;
+    d.core = a.core;
+    d.ctrl = a.ctrl;
+    d.e2 = a.e2;
+    d.min_pts = a.min_pts;
+    d.mode = a.mode;
+    return d;
+}
+
+template <int D>
+void run_pre(const ClusterArgs& a, cudaStream_t s)
+{
+    const size_t smem = sizeof(WarpMem<D>) * (size_t)(a.block / 32);
+    const int g = persistent_blocks<D>((const void*)k_pre<D>, a.block, smem);
+    k_pre<D><<<g, a.block, smem, s>>>(dev_args<D>(a));
+}
+
+template <int D>
+void run_main(const ClusterArgs& a, cudaStream_t s)
+{
+    const size_t smem = sizeof(WarpMem<D>) * (size_t)(a.block / 32);
+    const int g = persistent_blocks<D>((const void*)k_main<D>, a.block, smem);
+    k_main<D><<<g, a.block, smem, s>>>(dev_args<D>(a));
+}
+
+}  // namespace
+
+cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    int64_t gw = (a.m_cap * 32 + 255) / 256;
+    if (gw > 152 * 16) gw = 152 * 16;
+    k_init<<<(unsigned)gw, 256, 0, s>>>(a.leafr, a.ctrl, a.min_pts, a.labels, a.core);
+    note_launches(1);
+    if ((e = cudaMemsetAsync(a.canon, 0x7f, sizeof(int32_t) * (size_t)a.n, s)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
+{
+    if (a.min_pts <= 2) return cudaSuccess;  // Algorithm 3: no preprocessing for minPts <= 2
+    if (a.dim == 3) run_pre<3>(a, s); else run_pre<2>(a, s);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
+{
+    if (a.dim == 3) run_main<3>(a, s); else run_main<2>(a, s);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
+{
+    int64_t gn = (a.n + 255) / 256;
+    if (gn > 152 * 16) gn = 152 * 16;
+    k_finalize<<<(unsigned)gn, 256, 0, s>>>(a.labels, a.core, a.perm, a.n, a.canon);
+    k_relabel<<<(unsigned)gn, 256, 0, s>>>(a.labels, a.core, a.perm, a.n, a.mode, a.canon, labels_out, core_out);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace gbd

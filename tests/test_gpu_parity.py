@@ -1,0 +1,308 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small and medium inputs are compared with the full oracle clustering: core
+and noise sets and core labels exactly, border labels against their valid
+sets (tests/parity.py). The full-size 3D halo workload is checked at sampled
+points with brute-force neighbourhoods, and the two GPU algorithms must agree.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.parity import assert_matches_oracle, check_properties_at_samples
+from workloads import blobs, halo_eps, halos, roads, uniform
+
+torch = pytest.importorskip("torch")
+import paper_2103_05162_gb300 as gb  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = [gb.ALGO_FDBSCAN, gb.ALGO_DENSEBOX]
+MODES = [gb.MODE_DBSCAN, gb.MODE_DBSCAN_STAR]
+
+
+def run_gpu(X, eps, mp, mode, algo):
+    pts = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    lab, core = gb.dbscan_run(pts, eps, mp, mode=mode, algo=algo, want_core=True)
+    torch.cuda.synchronize()
+    gb.stream_status()
+    return lab.cpu().numpy(), core.cpu().numpy().astype(bool)
+
+
+def check(X, eps, mp, mode, algo, ref=None):
+    lab, core = run_gpu(X, eps, mp, mode, algo)
+    return assert_matches_oracle(X, eps, mp, mode, lab, core, ref), lab, core
+
+
+# ------------------------------------------------------------ config 0 family
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_blobs_16k_3d(seed, mode, algo):
+    """16384 3D points: 8 Gaussian blobs (sigma 0.02) + 10% noise, eps 0.03,
+    minPts 5 (the small 3D workload)."""
+    X = blobs(16384, 3, seed)
+    check(X, 0.03, 5, mode, algo)
+
+
+SMALL = []
+for s in range(40):
+    rs = np.random.default_rng(900 + s)
+    SMALL.append((s, int(rs.choice([2, 3])), int(rs.integers(1, 3000)), int(rs.choice([1, 2, 3, 5, 10])),
+                  int(rs.integers(0, 2)), float(np.float32(rs.uniform(0.01, 0.1)))))
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("seed,d,n,mp,mode,eps", SMALL)
+def test_small_random(seed, d, n, mp, mode, eps, algo):
+    X = blobs(n, d, seed, n_blobs=5, sigma=0.03)
+    check(X, eps, mp, mode, algo)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("seed", range(8))
+def test_lattice_exact_ties_and_duplicates(seed, algo):
+    """Integer lattice, eps = 1: many pairs exactly at distance eps, many
+    duplicates, dense cells of identical points."""
+    rs = np.random.default_rng(77 + seed)
+    d = 2 + seed % 2
+    X = rs.integers(0, 12, size=(int(rs.integers(100, 4000)), d)).astype(np.float32)
+    for mp in (1, 2, 4, 9):
+        for mode in MODES:
+            check(X, 1.0, mp, mode, algo)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_edge_cases(algo):
+    for mode in MODES:
+        # one point
+        check(np.zeros((1, 3), np.float32), 0.1, 1, mode, algo)
+        check(np.zeros((1, 2), np.float32), 0.1, 2, mode, algo)
+        # two points, adjacent and not
+        check(np.array([[0, 0], [1, 0]], np.float32), 1.0, 2, mode, algo)
+        check(np.array([[0, 0], [1.0000001, 0]], np.float32), 1.0, 2, mode, algo)
+        # minPts above n
+        check(blobs(500, 3, 5), 0.05, 501, mode, algo)
+        # all identical
+        check(np.full((777, 3), 0.5, np.float32), 1e-3, 10, mode, algo)
+        check(np.full((777, 2), -3.0, np.float32), 1e-3, 778, mode, algo)
+        # collinear 2D chain with spacing below eps
+        X = np.zeros((1000, 2), np.float32)
+        X[:, 0] = np.arange(1000, dtype=np.float32) * 0.5
+        check(X, 0.6, 3, mode, algo)
+        # ragged tails around the 32-point tile size
+        for n in (31, 32, 33, 63, 65, 1023, 1025):
+            check(blobs(n, 3, n), 0.08, 3, mode, algo)
+
+
+def test_empty_input():
+    pts = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    lab = gb.dbscan_run(pts, 0.1, 2)
+    assert lab.numel() == 0
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_offset_coordinates_tiny_eps(algo):
+    """Coordinates near 1e6 with eps of a few ulps: the grid arithmetic of
+    DenseBox loses precision (Sec. 4.2); results must stay exact."""
+    rs = np.random.default_rng(5)
+    base = np.float32(1e6)
+    ulp = np.spacing(base)
+    X = (base + ulp * rs.integers(0, 40, size=(3000, 3))).astype(np.float32)
+    for eps in (float(ulp), float(2.5 * ulp), float(7 * ulp)):
+        for mp in (2, 5, 20):
+            check(X, eps, mp, gb.MODE_DBSCAN, algo)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_nonfinite_input_is_rejected(algo):
+    X = blobs(1000, 3, 1)
+    X[17, 2] = np.nan
+    pts = torch.from_numpy(X).cuda()
+    with pytest.raises(gb.DbscanError) as e:
+        gb.dbscan_run(pts, 0.05, 3, algo=algo)
+    assert e.value.name == "NONFINITE"
+    X[17, 2] = np.inf
+    with pytest.raises(gb.DbscanError):
+        gb.dbscan_run(torch.from_numpy(X).cuda(), 0.05, 3, algo=algo)
+
+
+# ------------------------------------------------------- medium, full oracle
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("mp", [2, 10])
+def test_halos_256k(mp, algo):
+    """The 3D cosmology-like family at 2^18 points (eps = 0.2 x mean
+    spacing), full oracle comparison."""
+    n = 1 << 18
+    X = halos(n, 12, n_halos=800)
+    check(X, halo_eps(n), mp, gb.MODE_DBSCAN, algo)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_roads_512k(algo):
+    """The 2D GPS-trace-like family at 2^19 points; eps scaled with the
+    density so neighbourhoods keep their size."""
+    n = 1 << 19
+    X = roads(n, 3)
+    eps = float(np.float32(2e-4 * (4194304 / n) ** 0.5))
+    for mode in MODES:
+        check(X, eps, 10, mode, algo)
+
+
+def test_uniform_2d_and_3d_many_tiles():
+    for d, eps in ((2, 0.004), (3, 0.02)):
+        X = uniform(200_000, d, 9)
+        for algo in ALGOS:
+            check(X, eps, 4, gb.MODE_DBSCAN, algo)
+
+
+# ----------------------------------------------------------------- full size
+
+@pytest.mark.slow
+@pytest.mark.parametrize("algo", ALGOS)
+def test_roads_4m_full_oracle(algo):
+    """The 2D workload at full size (4,194,304 points, eps 2e-4, minPts 10),
+    compared with the full oracle clustering."""
+    X = roads(1 << 22, 1)
+    check(X, 2e-4, 10, gb.MODE_DBSCAN, algo)
+
+
+@pytest.fixture(scope="module")
+def halos16m():
+    n = 1 << 24
+    return halos(n, 2), halo_eps(n)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mp", [10, 2])
+def test_halos_16m_sampled(halos16m, mp):
+    """The 3D workload at full size (2^24 points, DenseBox, minPts 10 and 2):
+    properties at sampled points with brute-force neighbourhoods, and exact
+    agreement of the core set and core labels between DenseBox and FDbscan."""
+    X, eps = halos16m
+    lab, core = run_gpu(X, eps, mp, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX)
+    rs = np.random.default_rng(mp)
+    # samples: random points plus points in the densest regions (largest clusters)
+    samples = list(rs.choice(X.shape[0], 96, replace=False))
+    big = np.bincount(lab[lab >= 0]).argsort()[-8:]
+    for b in big:
+        members = np.nonzero(lab == b)[0]
+        samples += list(rs.choice(members, 4, replace=False))
+    check_properties_at_samples(X, eps, mp, gb.MODE_DBSCAN, lab, core, samples)
+    lab2, core2 = run_gpu(X, eps, mp, gb.MODE_DBSCAN, gb.ALGO_FDBSCAN)
+    assert (core == core2).all()
+    assert (lab[core] == lab2[core]).all()
+    assert ((lab == -1) == (lab2 == -1)).all()
+
+
+# ---------------------------------------------------------------- interfaces
+
+def test_repeat_runs_are_identical_on_unique_parts():
+    X = halos(1 << 17, 4, n_halos=400)
+    eps = halo_eps(1 << 17)
+    for algo in ALGOS:
+        a_lab, a_core = run_gpu(X, eps, 5, gb.MODE_DBSCAN, algo)
+        b_lab, b_core = run_gpu(X, eps, 5, gb.MODE_DBSCAN, algo)
+        assert (a_core == b_core).all()
+        assert (a_lab[a_core] == b_lab[a_core]).all()
+        assert ((a_lab == -1) == (b_lab == -1)).all()
+
+
+def test_host_entry_point_matches_device_entry_point():
+    X = blobs(50_000, 3, 8)
+    for algo in ALGOS:
+        d_lab, d_core = run_gpu(X, 0.02, 5, gb.MODE_DBSCAN_STAR, algo)
+        core = np.empty(X.shape[0], np.uint8)
+        h_lab, h_core = gb.dbscan_run_host(X, 0.02, 5, mode=gb.MODE_DBSCAN_STAR, algo=algo, core_out=core)
+        assert (h_lab == d_lab).all() and (h_core.astype(bool) == d_core).all()
+
+
+def test_tuning_does_not_change_results():
+    X = halos(1 << 16, 6, n_halos=200)
+    eps = halo_eps(1 << 16)
+    ref = oracle.dbscan(X, eps, 5, 0)
+    try:
+        for block, f in ((64, 1.0), (512, 0.5), (128, 0.25)):
+            gb.set_tuning(block, f)
+            for algo in ALGOS:
+                check(X, eps, 5, gb.MODE_DBSCAN, algo, ref=ref)
+    finally:
+        gb.set_tuning(0, 0.0)
+
+
+# ---------------------------------------------------------------- components
+
+def test_radix_sort_matches_stable_argsort():
+    rs = np.random.default_rng(1)
+    for n, bits in ((1, 8), (4095, 12), (4097, 36), (100_000, 64), (1 << 20, 30)):
+        keys = rs.integers(0, 1 << min(bits, 62), size=n, dtype=np.int64)
+        if bits == 64:
+            keys = rs.integers(-(1 << 62), 1 << 62, size=n, dtype=np.int64)
+        keys[::7] = keys[0]  # many duplicates: stability matters
+        vals = np.arange(n, dtype=np.int32)
+        k = torch.from_numpy(keys.copy()).cuda()
+        v = torch.from_numpy(vals.copy()).cuda()
+        gb.sort_pairs_u64(k, v, bits)
+        ku = keys.view(np.uint64) & np.uint64((1 << bits) - 1 if bits < 64 else 0xFFFFFFFFFFFFFFFF)
+        order = np.argsort(ku, kind="stable")
+        assert (v.cpu().numpy() == order).all()
+        assert (k.cpu().numpy() == keys[order]).all()
+
+
+def test_morton_codes_match_bit_interleave():
+    rs = np.random.default_rng(2)
+    for d, bits in ((3, 10), (2, 16), (3, 21), (2, 31)):
+        X = rs.uniform(-1, 3, size=(5000, d)).astype(np.float32)
+        lo, hi = X.min(0), X.max(0)
+        got = gb.morton_codes(torch.from_numpy(X).cuda(), lo, hi, bits).cpu().numpy().view(np.uint64)
+        cells = np.float32(2.0 ** bits)
+        for i in range(0, 5000, 37):
+            c = []
+            for k in range(d):
+                scale = cells / (hi[k] - lo[k])
+                t = np.floor((X[i, k] - lo[k]) * scale)
+                c.append(int(min(max(t, 0), 2 ** bits - 1)))
+            key = 0
+            for b in range(bits):
+                for k in range(d):
+                    key |= ((c[k] >> b) & 1) << (b * d + k)
+            assert int(got[i]) == key
+
+
+def test_lbvh_topology_reproduces_the_papers_figure():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pair_traversal_figure.json")))
+    keys = torch.tensor(g["leaf_keys"], dtype=torch.int64, device="cuda")
+    ch, rg = gb.lbvh_topology(keys)
+    ch = ch.cpu().numpy()
+    m = len(g["leaf_keys"])
+
+    def ref(r):
+        return m - 1 + int(r[1:]) if r[0] == "l" else int(r[1:])
+
+    for i, (a, b) in g["internal_children"].items():
+        assert tuple(ch[int(i)]) == (ref(a), ref(b)), i
+
+
+def test_lbvh_topology_invariants():
+    rs = np.random.default_rng(3)
+    for m in (2, 3, 17, 1000, 65537):
+        keys = np.sort(rs.integers(0, 1 << 20, size=m)).astype(np.int64)
+        keys[m // 3: m // 3 + m // 5] = keys[m // 3]  # duplicate run
+        ch, rg = gb.lbvh_topology(torch.from_numpy(keys).cuda())
+        ch, rg = ch.cpu().numpy(), rg.cpu().numpy()
+        seen = np.zeros(2 * m - 1, np.int64)
+        for i in range(m - 1):
+            for c in ch[i]:
+                seen[c] += 1
+        assert seen[0] == 0 and (seen[1:] == 1).all()  # every node but the root has one parent
+        assert tuple(rg[0]) == (0, m - 1)
+        for i in range(m - 1):
+            lo, hi = rg[i]
+            l, r = ch[i]
+            llo, lhi = (l - (m - 1),) * 2 if l >= m - 1 else tuple(rg[l])
+            rlo, rhi = (r - (m - 1),) * 2 if r >= m - 1 else tuple(rg[r])
+            assert llo == lo and rhi == hi and lhi + 1 == rlo
