@@ -112,8 +112,11 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- workload
 def workload(n: int, seed: int):
+    """The 3D halo family; below 2^24 points the number of halos shrinks in
+    proportion so that the halo size distribution is kept."""
     from workloads import halo_eps, halos
-    return halos(n, seed), halo_eps(n)
+    n_halos = max(10, round(50000 * n / (1 << 24)))
+    return halos(n, seed, n_halos=n_halos), halo_eps(n)
 
 
 def workload_desc(n: int, eps: float, min_pts: int) -> str:

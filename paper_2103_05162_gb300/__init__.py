@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
             "dbscan_release_workspaces": [],
             "dbscan_set_tuning": [i32, f32],
             "dbscan_sort_pairs_u64": [vp, vp, i64, i32, vp],
+            "dbscan_sort_pairs_u64_noalloc": [vp, vp, i64, i32, vp],
             "dbscan_morton_codes": [vp, i64, i32, vp, vp, i32, vp, vp],
             "dbscan_lbvh_topology": [vp, i64, vp, vp, vp],
             "dbscan_profile_enable": [i32],
@@ -251,6 +252,17 @@ def sort_pairs_u64(keys, values, key_bits: int, stream=None):
     lib = load()
     _check(lib.dbscan_sort_pairs_u64(_ptr(keys), _ptr(values), keys.numel(), int(key_bits),
                                      _stream_handle(stream, keys.device)))
+
+
+SORT_NOALLOC_MAX_PAIRS = 1 << 20
+
+
+def sort_pairs_u64_noalloc(keys, values, key_bits: int, stream=None):
+    """sort_pairs_u64 without any device allocation (scratch in a static
+    device array; n <= SORT_NOALLOC_MAX_PAIRS; overlapping calls race)."""
+    lib = load()
+    _check(lib.dbscan_sort_pairs_u64_noalloc(_ptr(keys), _ptr(values), keys.numel(), int(key_bits),
+                                             _stream_handle(stream, keys.device)))
 
 
 def morton_codes(points, lo, hi, bits: int, out=None, stream=None):
