@@ -214,26 +214,73 @@ __global__ void k_cell_dense(const typename Traits<D>::Point* __restrict__ sp, c
     }
 }
 
-// per point: dense flag and segment boundary marker (first point of a run of
-// non-dense points) for the max-scan
-__global__ void k_point_flags(const int32_t* __restrict__ cellid, const uint8_t* __restrict__ cdense, int64_t n,
-                              uint8_t* __restrict__ pdense, int32_t* __restrict__ bnd)
+// per point: 0 outside dense cells, 1 in a dense cell that fits in a tile
+// (at most TILE points: it stays inside a tile, pre-united and core), 2 in a
+// larger dense cell (one BVH leaf of its own, queried as a box)
+__global__ void k_point_flags(const int32_t* __restrict__ cellid, const int32_t* __restrict__ cstart,
+                              const uint8_t* __restrict__ cdense, int64_t n, uint8_t* __restrict__ pdense)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool d = cdense[cellid[i] - 1] != 0;
-        const bool prev_d = i > 0 ? cdense[cellid[i - 1] - 1] != 0 : true;
-        pdense[i] = d ? 1 : 0;
-        bnd[i] = (!d && prev_d) ? (int32_t)i : -1;
+        const int c = cellid[i] - 1;
+        uint8_t f = 0;
+        if (cdense[c]) f = (cstart[c + 1] - cstart[c] > TILE) ? 2 : 1;
+        pdense[i] = f;
     }
 }
 
-// leaf starts: the first point of every dense cell, and every TILE-th point of
-// each run of non-dense points (counted from the run's start)
-__global__ void k_leaf_flags(const int32_t* __restrict__ head, const uint8_t* __restrict__ pdense,
-                             const int32_t* __restrict__ segstart, int64_t n, int32_t* __restrict__ lf)
+// Common-prefix length of sorted keys i and j (-1 outside [0, n)), equal keys
+// told apart by index: the delta of Karras (2012).
+template <typename K>
+__device__ __forceinline__ int kdelta_t(const K* __restrict__ k, int64_t n, int64_t i, int64_t j)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        lf[i] = pdense[i] ? head[i] : (((i - segstart[i]) % TILE) == 0 ? 1 : 0);
+    if (j < 0 || j >= n) return -1;
+    const K a = k[i], b = k[j];
+    constexpr int KB = 8 * (int)sizeof(K);
+    if (a != b) return sizeof(K) == 8 ? __clzll((long long)(a ^ b)) : __clz((int)(a ^ b));
+    return KB + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+// Does the radix-tree node that splits points g and g+1 cover more than T
+// points? Its range is the run of keys sharing at least delta(g, g+1) leading
+// bits with key g; the run is found by binary search within T of g on each
+// side (reaching a window's end already means more than T).
+template <typename K>
+__device__ __forceinline__ bool radix_split_exceeds(const K* __restrict__ k, int64_t n, int64_t g, int T)
+{
+    const int d = kdelta_t(k, n, g, g + 1);
+    int64_t lo = g - T < 0 ? 0 : g - T, hi = g;  // smallest j in [lo, g] with delta(g, j) >= d
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (kdelta_t(k, n, g, mid) >= d) hi = mid; else lo = mid + 1;
+    }
+    const int64_t a = lo;
+    lo = g + 1;
+    hi = g + 1 + T > n - 1 ? n - 1 : g + 1 + T;  // largest j in [g+1, hi] with delta(g, j) >= d
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (kdelta_t(k, n, g, mid) >= d) lo = mid; else hi = mid - 1;
+    }
+    const int64_t b = lo;
+    return (b - a + 1) > T;
+}
+
+// leaf starts: the first point of every dense cell larger than a tile;
+// elsewhere a new tile starts after such a cell and wherever the radix-tree
+// node splitting two neighbours covers more than T points. Tiles are then the maximal
+// subtrees of at most T points (spatially compact, unlike fixed runs of T in
+// Morton order, which can straddle a jump of the curve).
+template <typename K>
+__global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ head,
+                             const uint8_t* __restrict__ pdense, int64_t n, int T, int32_t* __restrict__ lf)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int f;
+        if (i == 0) f = 1;
+        else if (pdense && pdense[i] == 2) f = head[i];
+        else if (pdense && pdense[i - 1] == 2) f = 1;
+        else f = radix_split_exceeds(keys, n, i - 1, T) ? 1 : 0;
+        lf[i] = f;
+    }
 }
 
 // lidx = exclusive scan of lf; writes leaf starts and m
@@ -251,30 +298,18 @@ __global__ void k_leaf_write(const int32_t* __restrict__ lf, const int32_t* __re
 }
 
 // leaf records (start, end | dense << 31) and the leaf keys
+template <typename K>
 __global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t* __restrict__ pdense,
-                               const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ctrl,
+                               const K* __restrict__ keys, const uint32_t* __restrict__ ctrl,
                                int2* __restrict__ leafr, uint64_t* __restrict__ lkey)
 {
     const int64_t m = ctrl[CTRL_M];
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = lstart[l], e = lstart[l + 1];
-        const uint32_t dense = pdense[s];
+        const uint32_t dense = (pdense && pdense[s] == 2) ? 1u : 0u;
         leafr[l] = make_int2(s, (int32_t)((uint32_t)e | (dense << 31)));
-        lkey[l] = keys[s];
+        lkey[l] = (uint64_t)keys[s];
     }
-}
-
-// FDBSCAN leaves: tiles of TILE consecutive sorted points
-__global__ void k_tile_records(const uint32_t* __restrict__ keys32, int64_t n, int64_t m, int2* __restrict__ leafr,
-                               uint64_t* __restrict__ lkey, uint32_t* __restrict__ ctrl)
-{
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = l * TILE;
-        const int64_t e = s + TILE < n ? s + TILE : n;
-        leafr[l] = make_int2((int32_t)s, (int32_t)e);
-        lkey[l] = keys32[s];
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[CTRL_M] = (uint32_t)m;
 }
 
 // ---------------------------------------------------------------------------
@@ -456,21 +491,26 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
         k_cell_dense<3><<<gw, 256, 0, s>>>(static_cast<const float4*>(sp), t.cstart, ctrl, min_pts, e2, t.cdense);
     else
         k_cell_dense<2><<<gw, 256, 0, s>>>(static_cast<const float2*>(sp), t.cstart, ctrl, min_pts, e2, t.cdense);
-    k_point_flags<<<g, 256, 0, s>>>(t.cellid, t.cdense, n, t.pdense, t.bnd);
-    if ((e = scan_i32(t.bnd, t.segstart, n, SCAN_MAX, true, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_flags<<<g, 256, 0, s>>>(t.head, t.pdense, t.segstart, n, t.lf);
+    k_point_flags<<<g, 256, 0, s>>>(t.cellid, t.cstart, t.cdense, n, t.pdense);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.head, t.pdense, n, TILE, t.lf);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, leafr, lkey);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, leafr, lkey);
     note_launches(7);
     return cudaGetLastError();
 }
 
-void launch_tile_leaves(const uint32_t* keys32, int64_t n, int64_t m, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
-                        cudaStream_t s)
+cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBoxTemps& t, int2* leafr,
+                               uint64_t* lkey, uint32_t* ctrl, cudaStream_t s)
 {
-    k_tile_records<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(keys32, n, m, leafr, lkey, ctrl);
-    note_launches(1);
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    cudaError_t e;
+    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, TILE, t.lf);
+    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
+    k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, leafr, lkey);
+    note_launches(3);
+    return cudaGetLastError();
 }
 
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,

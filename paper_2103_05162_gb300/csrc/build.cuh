@@ -36,9 +36,7 @@ struct DenseBoxTemps {
     int32_t* cellid;    // n
     int32_t* cstart;    // n + 1
     uint8_t* cdense;    // n
-    uint8_t* pdense;    // n
-    int32_t* bnd;       // n
-    int32_t* segstart;  // n
+    uint8_t* pdense;    // n: 0 not dense, 1 dense cell within a tile, 2 dense cell as its own leaf
     int32_t* lf;        // n
     int32_t* lidx;      // n
     int32_t* lstart;    // n + 1
@@ -56,8 +54,8 @@ void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, v
 cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t n, int dim, int min_pts, float e2,
                                    const DenseBoxTemps& t, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
                                    cudaStream_t s);
-void launch_tile_leaves(const uint32_t* keys32, int64_t n, int64_t m, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
-                        cudaStream_t s);
+cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBoxTemps& t, int2* leafr,
+                               uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
                  int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s);
 void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* parent, int2* child_out,
@@ -69,6 +67,10 @@ struct ClusterArgs {
     const void* nodes;     // m-1 node records
     const void* nodebox;   // 2m-1 boxes (leaf boxes at m-1+l)
     const int2* leafr;     // m leaf records
+    uint8_t* lsolid;       // m: 1 if all points of the leaf are core and in one set
+    const uint8_t* pdense; // n or null: dense-cell flags per sorted point (DenseBox)
+    const int32_t* cellid; // n or null: 1-based cell of each sorted point
+    const int32_t* cstart; // cells + 1 or null: first point of each cell
     const uint32_t* perm;  // sorted position -> input index
     int32_t* labels;       // n (union-find parents, sorted index space)
     uint8_t* core;         // n (sorted order)

@@ -135,12 +135,17 @@ struct Plan {
     int4* nmeta;
     int32_t* parent;
     int32_t* visit;
+    uint8_t* lsolid;
     int32_t* labels;
     uint8_t* core;
     int32_t* canon;
 };
 
-int64_t leaf_cap(int64_t n, int algo) { return algo == DBSCAN_ALGO_FDBSCAN ? (n + TILE - 1) / TILE : n; }
+int64_t leaf_cap(int64_t n, int algo)
+{
+    (void)algo;
+    return n;  // tiles hold 1..TILE points, dense cells any number
+}
 
 size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
 {
@@ -164,15 +169,13 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
         p.db.cstart = c.take<int32_t>(n + 1);
         p.db.cdense = c.take<uint8_t>(n);
         p.db.pdense = c.take<uint8_t>(n);
-        p.db.bnd = c.take<int32_t>(n);
-        p.db.segstart = c.take<int32_t>(n);
-        p.db.lf = c.take<int32_t>(n);
-        p.db.lidx = c.take<int32_t>(n);
-        p.db.lstart = c.take<int32_t>(n + 1);
-        p.db.scan_temp = c.take<int32_t>(scan_temp_words(n));
     } else {
         p.db = DenseBoxTemps{};
     }
+    p.db.lf = c.take<int32_t>(n);
+    p.db.lidx = c.take<int32_t>(n);
+    p.db.lstart = c.take<int32_t>(n + 1);
+    p.db.scan_temp = c.take<int32_t>(scan_temp_words(n));
     p.leafr = c.take<int2>(mc);
     p.lkey = c.take<uint64_t>(mc);
     p.nodebox = c.take<char>(box * (size_t)(2 * mc));
@@ -180,6 +183,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
     p.nmeta = c.take<int4>(mc);
     p.parent = c.take<int32_t>(2 * mc);
     p.visit = c.take<int32_t>(mc);
+    p.lsolid = c.take<uint8_t>(mc);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.canon = c.take<int32_t>(n);
@@ -381,7 +385,7 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
         launch_gather(points, perm, n, dim, p.sp, s);
         T.end();
         T.begin(ST_LEAVES);
-        launch_tile_leaves(keys_sorted, n, m_cap, p.leafr, p.lkey, p.ctrl, s);
+        TRY_CUDA(launch_tile_leaves(keys_sorted, n, p.db, p.leafr, p.lkey, p.ctrl, s));
         T.end();
     } else {
         int key_bits = 0;
@@ -413,6 +417,10 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     a.nodes = p.nodes;
     a.nodebox = p.nodebox;
     a.leafr = p.leafr;
+    a.lsolid = p.lsolid;
+    a.pdense = algo == DBSCAN_ALGO_DENSEBOX ? p.db.pdense : nullptr;
+    a.cellid = algo == DBSCAN_ALGO_DENSEBOX ? p.db.cellid : nullptr;
+    a.cstart = algo == DBSCAN_ALGO_DENSEBOX ? p.db.cstart : nullptr;
     a.perm = perm;
     a.labels = p.labels;
     a.core = p.core;

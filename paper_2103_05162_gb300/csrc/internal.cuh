@@ -118,6 +118,24 @@ template <> struct Traits<3> {
     }
     // diameter test of a box: the squared distance of its corners
     __device__ static __forceinline__ float diag2(const Box& b) { return dist2(b.lo, b.hi); }
+    // squared distance from p to the farthest corner of b: an upper bound of
+    // dist2(p, y) for every y in b (the same monotone-rounding argument), so
+    // <= e2 means every point of b is within eps of p
+    __device__ static __forceinline__ float far_dist2(const Point& p, const Box& b)
+    {
+        float s = sqr_rn(fmaxf(__fsub_rn(p.x, b.lo.x), __fsub_rn(b.hi.x, p.x)));
+        s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(p.y, b.lo.y), __fsub_rn(b.hi.y, p.y))));
+        s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(p.z, b.lo.z), __fsub_rn(b.hi.z, p.z))));
+        return s;
+    }
+    // the same between two boxes: every pair (a in A, b in B) is within it
+    __device__ static __forceinline__ float box_far2(const Box& a, const Box& b)
+    {
+        float s = sqr_rn(fmaxf(__fsub_rn(b.hi.x, a.lo.x), __fsub_rn(a.hi.x, b.lo.x)));
+        s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(b.hi.y, a.lo.y), __fsub_rn(a.hi.y, b.lo.y))));
+        s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(b.hi.z, a.lo.z), __fsub_rn(a.hi.z, b.lo.z))));
+        return s;
+    }
     __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
     {
         Node n;
@@ -179,6 +197,18 @@ template <> struct Traits<2> {
     __device__ static __forceinline__ float diag2(const Box& b)
     {
         return dist2(make_float2(b.lo.x, b.lo.y), make_float2(b.hi.x, b.hi.y));
+    }
+    __device__ static __forceinline__ float far_dist2(const Point& p, const Box& b)
+    {
+        float s = sqr_rn(fmaxf(__fsub_rn(p.x, b.lo.x), __fsub_rn(b.hi.x, p.x)));
+        s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(p.y, b.lo.y), __fsub_rn(b.hi.y, p.y))));
+        return s;
+    }
+    __device__ static __forceinline__ float box_far2(const Box& a, const Box& b)
+    {
+        float s = sqr_rn(fmaxf(__fsub_rn(b.hi.x, a.lo.x), __fsub_rn(a.hi.x, b.lo.x)));
+        s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(b.hi.y, a.lo.y), __fsub_rn(a.hi.y, b.lo.y))));
+        return s;
     }
     __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
     {

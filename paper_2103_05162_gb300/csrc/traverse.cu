@@ -3,24 +3,32 @@
 // final compression (Sec. 4.3) and canonical relabelling.
 //
 // Work is organised per BVH leaf and per warp: a leaf is either a tile of up
-// to 32 consecutive sorted points outside dense cells (one point per lane) or
-// a whole dense cell (Sec. 4.2). A warp takes the next leaf from a global
-// counter (persistent kernels), and its 32 lanes traverse the tree together
-// with one shared stack: at each node every lane tests its own point against
-// both children's boxes (stored in the node record) and the warp descends
-// where any lane hits. At a leaf, pairs are tested either lane-per-query
-// (looping over the leaf's points) or lane-per-leaf-point (looping over the
-// queries that reached the leaf), whichever needs fewer steps.
+// to 32 sorted points outside dense cells (one point per lane) or a whole
+// dense cell (Sec. 4.2). A warp takes the next leaf from a global counter
+// (persistent kernels), and its 32 lanes traverse the tree together with one
+// shared stack: at each node every lane tests its own point against both
+// children's boxes (stored in the node record) and the warp descends where
+// any lane hits. At a leaf, pairs are tested either lane-per-query (looping
+// over the leaf's points) or lane-per-leaf-point (looping over the queries
+// that reached the leaf), whichever needs fewer steps.
+//
+// Two exact shortcuts cut the pair tests in dense regions:
+//  * containment: when the farthest corner of a leaf's box is within eps of a
+//    query, every point of the leaf is a neighbour (no per-point tests);
+//  * solid leaves: a leaf whose points are all core and already one set
+//    (every dense cell, and every tile that becomes so after its own pairs
+//    are united) behaves like a dense cell of Sec. 4.2: one adjacent pair
+//    decides, and nothing is tested when the two sides already share a root.
 //
 // Preprocessing (minPts > 2 only): each point outside dense cells counts its
 // neighbours (itself included) and stops at minPts; points of dense cells are
 // core by construction.
-// Main: each leaf visits only the leaves with index >= its own (the pair mask
+// Intra: each tile unites its own pairs and records whether it is solid.
+// Main: each leaf visits only the leaves with index > its own (the pair mask
 // of Sec. 4.1, Figure "pair traversal"), so every pair is seen once, and
 // applies the rule of Algorithm 3 as it finds each pair, with no neighbour
 // list: core-core pairs are united, a core point claims a non-core neighbour
-// with one compare-and-swap (Sec. 3.2). A dense cell needs only one adjacent
-// point to be found (Sec. 4.2).
+// with one compare-and-swap (Sec. 3.2).
 #include "build.cuh"
 
 namespace gbd {
@@ -37,6 +45,14 @@ template <> struct NB<3> {
         T::Node r;
         r.a = __ldg(&n[i].a); r.b = __ldg(&n[i].b); r.c = __ldg(&n[i].c); r.m = __ldg(&n[i].m);
         return r;
+    }
+    __device__ static __forceinline__ T::Box box_l(const T::Node& n)
+    {
+        return T::Box{make_float4(n.a.x, n.a.y, n.a.z, 0.f), make_float4(n.a.w, n.b.x, n.b.y, 0.f)};
+    }
+    __device__ static __forceinline__ T::Box box_r(const T::Node& n)
+    {
+        return T::Box{make_float4(n.b.z, n.b.w, n.c.x, 0.f), make_float4(n.c.y, n.c.z, n.c.w, 0.f)};
     }
     __device__ static __forceinline__ float pl(const T::Node& n, const T::Point& p)
     {
@@ -66,6 +82,14 @@ template <> struct NB<2> {
         T::Node r;
         r.a = __ldg(&n[i].a); r.b = __ldg(&n[i].b); r.m = __ldg(&n[i].m);
         return r;
+    }
+    __device__ static __forceinline__ T::Box box_l(const T::Node& n)
+    {
+        return T::Box{make_float4(n.a.x, n.a.y, 0.f, 0.f), make_float4(n.a.z, n.a.w, 0.f, 0.f)};
+    }
+    __device__ static __forceinline__ T::Box box_r(const T::Node& n)
+    {
+        return T::Box{make_float4(n.b.x, n.b.y, 0.f, 0.f), make_float4(n.b.z, n.b.w, 0.f, 0.f)};
     }
     __device__ static __forceinline__ float pl(const T::Node& n, const T::Point& p)
     {
@@ -97,15 +121,19 @@ struct WarpMem {
 };
 
 // Warp-cooperative stack traversal. Children whose last leaf is below
-// v.mask_lo are never entered (the pair mask). Returns when the stack is
-// empty or when v.leaf() asks to stop (early termination).
+// v.mask_lo are never entered (the pair mask). v.leaf(L, mask, box) gets the
+// lanes that reached leaf L and its box; it returns true to stop early.
 template <int D, class V>
-__device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes, int64_t m, V& v,
+__device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes,
+                                         const typename Traits<D>::Box* __restrict__ nodebox, int64_t m, V& v,
                                          int* stack, uint32_t* ctrl)
 {
     const int lane = threadIdx.x & 31;
     if (m == 1) {
-        v.leaf(0, v.root_mask());
+        typename Traits<D>::Box b;
+        b.lo = nodebox[0].lo;
+        b.hi = nodebox[0].hi;
+        v.leaf(0, v.root_mask(), b);
         return;
     }
     const int leaf0 = (int)(m - 1);
@@ -125,14 +153,14 @@ __device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restr
         int next = -1;
         if (ml) {
             if (nd.m.x >= leaf0) {
-                if (v.leaf(nd.m.x - leaf0, ml)) return;
+                if (v.leaf(nd.m.x - leaf0, ml, NB<D>::box_l(nd))) return;
             } else {
                 next = nd.m.x;
             }
         }
         if (mr) {
             if (nd.m.y >= leaf0) {
-                if (v.leaf(nd.m.y - leaf0, mr)) return;
+                if (v.leaf(nd.m.y - leaf0, mr, NB<D>::box_r(nd))) return;
             } else if (next < 0) {
                 next = nd.m.y;
             } else {
@@ -175,11 +203,18 @@ struct PreV {
     __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return act && NB<D>::pr(n, p) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, act); }
 
-    __device__ bool leaf(int L, unsigned mask)
+    __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
     {
         const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
         mask &= __ballot_sync(FULL, act);
+        // the whole leaf within eps: count it at once
+        const bool cont = ((mask >> lane) & 1u) && T::far_dist2(p, box) <= e2;
+        if (cont) {
+            cnt += e - s;
+            if (cnt >= min_pts) act = false;
+        }
+        mask &= ~__ballot_sync(FULL, cont);
         for (int c = s; c < e && mask; c += 32) {
             const int k = min(32, e - c);
             if (__popc(mask) < k) {
@@ -244,14 +279,14 @@ struct Rule {
             else if (bcore) uf_claim(labels, a, b);
         }
     }
-    // would point x (core flag xcore) change anything by joining the dense
-    // cell whose first point is s?
-    __device__ __forceinline__ bool need_dense(int x, bool xcore, int s) const
+    // would point x (core flag xcore) change anything by joining the solid
+    // leaf whose first point is s?
+    __device__ __forceinline__ bool need_solid(int x, bool xcore, int s) const
     {
         if (min_pts <= 2 || xcore) return uf_find(labels, x) != uf_find(labels, s);
         return mode == DBSCAN_MODE_DBSCAN && __ldcg(labels + x) == x;
     }
-    __device__ __forceinline__ void join_dense(int x, bool xcore, int s) const
+    __device__ __forceinline__ void join_solid(int x, bool xcore, int s) const
     {
         if (min_pts <= 2 || xcore) {
             if (min_pts == 2) core[x] = 1;
@@ -262,19 +297,20 @@ struct Rule {
     }
 };
 
-// Main visitor for a tile of points outside dense cells (one point per lane).
+// Main visitor for a tile that is not solid (one point per lane).
 template <int D>
 struct MainPtV {
     using T = Traits<D>;
     using P = typename T::Point;
     const P* __restrict__ sp;
     const int2* __restrict__ leafr;
+    const uint8_t* __restrict__ lsolid;
     const uint8_t* core;
     P* buf;
     uint8_t* cbuf;
     Rule rule;
     float e2;
-    int mask_lo;  // = own leaf index
+    int mask_lo;  // = own leaf index + 1: only leaves after this one
     int lane;
     int sQ;       // first point of own leaf
     P p;
@@ -286,23 +322,13 @@ struct MainPtV {
     __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return valid && NB<D>::pr(n, p) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
-    __device__ bool leaf(int L, unsigned mask)
+    __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
     {
+        if (L < mask_lo) return false;
         const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
-        const bool dense = r.y < 0;
-        if (L == mask_lo) {
-            // own tile: the pairs (q, q') with q' > q
-            const int k = e - s;
-            if (lane < k) { buf[lane] = p; cbuf[lane] = qcore ? 1 : 0; }
-            __syncwarp();
-            if (valid)
-                for (int u = lane + 1; u < k; ++u)
-                    if (dist2(p, buf[u]) <= e2) rule.pair(q, qcore, s + u, cbuf[u] != 0);
-            __syncwarp();
-            return false;
-        }
-        if (!dense) {
+        const bool cont = ((mask >> lane) & 1u) && T::far_dist2(p, box) <= e2;
+        if (!lsolid[L]) {
             const int k = e - s;
             if (__popc(mask) < k) {
                 const bool in = lane < k;
@@ -315,7 +341,8 @@ struct MainPtV {
                     mm &= mm - 1;
                     const P pq = NB<D>::shfl(p, qq);
                     const bool qc = __shfl_sync(FULL, qcore, qq);
-                    if (in && dist2(pq, rp) <= e2) rule.pair(sQ + qq, qc, ri, rc);
+                    const bool qcont = __shfl_sync(FULL, cont, qq);
+                    if (in && (qcont || dist2(pq, rp) <= e2)) rule.pair(sQ + qq, qc, ri, rc);
                     __syncwarp();
                 }
             } else {
@@ -323,15 +350,16 @@ struct MainPtV {
                 __syncwarp();
                 if ((mask >> lane) & 1u)
                     for (int u = 0; u < k; ++u)
-                        if (dist2(p, buf[u]) <= e2) rule.pair(q, qcore, s + u, cbuf[u] != 0);
+                        if (cont || dist2(p, buf[u]) <= e2) rule.pair(q, qcore, s + u, cbuf[u] != 0);
                 __syncwarp();
             }
             return false;
         }
-        // dense cell: one adjacent point decides (all its points are core and
-        // already one set rooted at its first point s)
-        const bool need = ((mask >> lane) & 1u) && rule.need_dense(q, qcore, s);
-        unsigned nm = __ballot_sync(FULL, need);
+        // solid leaf: one adjacent point decides (its points are all core and
+        // already one set rooted at that of its first point s)
+        const bool need = ((mask >> lane) & 1u) && rule.need_solid(q, qcore, s);
+        if (need && cont) rule.join_solid(q, qcore, s);
+        unsigned nm = __ballot_sync(FULL, need && !cont);
         while (nm) {
             const int qq = __ffs(nm) - 1;
             nm &= nm - 1;
@@ -342,26 +370,109 @@ struct MainPtV {
                 const bool h = j < e && dist2(pq, sp[j]) <= e2;
                 if (__any_sync(FULL, h)) { found = true; break; }
             }
-            if (found && lane == qq) rule.join_dense(q, qcore, s);
+            if (found && lane == qq) rule.join_solid(q, qcore, s);
             __syncwarp();
         }
         return false;
     }
 };
 
-// Main visitor for a dense cell as the query (its box is tested against the
-// nodes; its points are all core and already one set).
+// Main visitor for a solid tile (one point per lane, all core, one set): the
+// traversal keeps per-lane point tests; at a leaf one adjacent pair decides.
+template <int D>
+struct MainSolidV {
+    using T = Traits<D>;
+    using P = typename T::Point;
+    const P* __restrict__ sp;
+    const int2* __restrict__ leafr;
+    const uint8_t* __restrict__ lsolid;
+    const uint8_t* core;
+    P* buf;
+    Rule rule;
+    float e2;
+    int mask_lo;  // = own leaf index + 1
+    int lane;
+    int sQ;
+    P p;
+    bool valid;
+    typename T::Box qb;
+
+    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return valid && NB<D>::pl(n, p) <= e2; }
+    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return valid && NB<D>::pr(n, p) <= e2; }
+    __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
+
+    __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
+    {
+        if (L < mask_lo) return false;
+        const int2 r = __ldg(&leafr[L]);
+        const int s = r.x, e = r.y & 0x7fffffff;
+        if (lsolid[L]) {
+            int same = 0;
+            if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
+            if (__shfl_sync(FULL, same, 0)) return false;
+            bool found = __any_sync(FULL, ((mask >> lane) & 1u) && T::far_dist2(p, box) <= e2);
+            for (int c = s; c < e && !found; c += 32) {
+                const int k = min(32, e - c);
+                if (__popc(mask) < k) {
+                    const bool in = lane < k;
+                    const P rp = in ? sp[c + lane] : sp[c];
+                    unsigned mm = mask;
+                    while (mm && !found) {
+                        const int qq = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const P pq = NB<D>::shfl(p, qq);
+                        found = __any_sync(FULL, in && dist2(pq, rp) <= e2);
+                    }
+                } else {
+                    if (lane < k) buf[lane] = sp[c + lane];
+                    __syncwarp();
+                    bool h = false;
+                    if ((mask >> lane) & 1u)
+                        for (int u = 0; u < k; ++u)
+                            if (dist2(p, buf[u]) <= e2) { h = true; break; }
+                    __syncwarp();
+                    found = __any_sync(FULL, h);
+                }
+            }
+            if (found && lane == 0) uf_union(rule.labels, sQ, s);
+            __syncwarp();
+            return false;
+        }
+        // a tile that is not solid: one lane per tile point
+        const int k = e - s;
+        const bool in = lane < k;
+        const int ri = s + lane;
+        const P rp = in ? sp[ri] : sp[s];
+        const bool rc = in && core[ri];
+        const bool need = in && rule.need_solid(ri, rc, sQ);
+        bool found = need && T::far_dist2(rp, qb) <= e2;
+        unsigned mm = mask;
+        while (mm && __any_sync(FULL, need && !found)) {
+            const int qq = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const P pq = NB<D>::shfl(p, qq);
+            if (need && !found && dist2(rp, pq) <= e2) found = true;
+        }
+        if (need && found) rule.join_solid(ri, rc, sQ);
+        __syncwarp();
+        return false;
+    }
+};
+
+// Main visitor for a dense cell larger than a tile as the query:
+// its box is tested against the nodes; its points are all core and one set.
 template <int D>
 struct MainBoxV {
     using T = Traits<D>;
     using P = typename T::Point;
     const P* __restrict__ sp;
     const int2* __restrict__ leafr;
+    const uint8_t* __restrict__ lsolid;
     const uint8_t* core;
     P* buf;
     Rule rule;
     float e2;
-    int mask_lo;  // = own leaf index
+    int mask_lo;  // = own leaf index + 1
     int lane;
     int sQ, eQ;
     typename T::Box qb;
@@ -370,17 +481,17 @@ struct MainBoxV {
     __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return NB<D>::br(n, qb) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return FULL; }
 
-    __device__ bool leaf(int L, unsigned)
+    __device__ bool leaf(int L, unsigned, const typename T::Box& box)
     {
-        if (L == mask_lo) return false;
+        if (L < mask_lo) return false;
         const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
-        const bool dense = r.y < 0;
-        if (dense) {
+        if (lsolid[L]) {
+            // solid against solid: any adjacent cross pair unites the two sets
             int same = 0;
             if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
             if (__shfl_sync(FULL, same, 0)) return false;
-            bool found = false;
+            bool found = T::box_far2(qb, box) <= e2;
             for (int cq = sQ; cq < eQ && !found; cq += 32) {
                 const int iq = cq + lane;
                 const bool inq = iq < eQ;
@@ -401,14 +512,14 @@ struct MainBoxV {
             __syncwarp();
             return false;
         }
-        // a tile of points outside dense cells: one lane per point
+        // a tile that is not solid: one lane per tile point
         const int k = e - s;
         const bool in = lane < k;
         const int ri = s + lane;
         const P rp = in ? sp[ri] : sp[s];
         const bool rc = in && core[ri];
-        const bool need = in && rule.need_dense(ri, rc, sQ);
-        bool found = false;
+        const bool need = in && rule.need_solid(ri, rc, sQ);
+        bool found = need && T::far_dist2(rp, qb) <= e2;
         for (int cq = sQ; cq < eQ; cq += 32) {
             if (!__any_sync(FULL, need && !found)) break;
             const int kq = min(32, eQ - cq);
@@ -419,7 +530,7 @@ struct MainBoxV {
                     if (dist2(rp, buf[u]) <= e2) { found = true; break; }
             __syncwarp();
         }
-        if (need && found) rule.join_dense(ri, rc, sQ);
+        if (need && found) rule.join_solid(ri, rc, sQ);
         __syncwarp();
         return false;
     }
@@ -431,6 +542,7 @@ struct DevArgs {
     const typename Traits<D>::Node* nodes;
     const typename Traits<D>::Box* nodebox;
     const int2* leafr;
+    uint8_t* lsolid;
     int32_t* labels;
     uint8_t* core;
     uint32_t* ctrl;
@@ -460,14 +572,55 @@ __global__ void k_pre(DevArgs<D> a)
         if (r.y < 0) continue;  // dense cell: all core already
         const int s = r.x, e = r.y;
         const int q = s + lane;
+        // points of dense cells inside the tile are core already
+        const bool counts = q < e && !a.core[q];
+        if (!__any_sync(FULL, counts)) continue;
         PreV<D> v;
         v.sp = a.sp; v.leafr = a.leafr; v.buf = wm->buf; v.e2 = a.e2; v.min_pts = a.min_pts;
         v.mask_lo = 0; v.lane = lane;
-        v.act = q < e;
-        v.p = a.sp[v.act ? q : s];
+        v.act = counts;
+        v.p = a.sp[q < e ? q : s];
         v.cnt = 0;
-        traverse<D>(a.nodes, m, v, wm->stack, a.ctrl);
-        if (q < e) a.core[q] = v.cnt >= a.min_pts ? 1 : 0;
+        traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+        if (counts) a.core[q] = v.cnt >= a.min_pts ? 1 : 0;
+    }
+}
+
+// Each tile unites its own pairs (q, q') with q' > q, then records whether it
+// is solid: all its points core and in one set. Dense cells are solid.
+template <int D>
+__global__ void k_intra(DevArgs<D> a)
+{
+    using P = typename Traits<D>::Point;
+    const int lane = threadIdx.x & 31;
+    const int64_t m = a.ctrl[CTRL_M];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const Rule rule{a.labels, a.core, a.min_pts, a.mode};
+    for (int64_t L = wid; L < m; L += nw) {
+        const int2 r = a.leafr[L];
+        if (r.y < 0) {
+            if (lane == 0) a.lsolid[L] = 1;
+            continue;
+        }
+        const int s = r.x, k = r.y - r.x;
+        const int q = s + lane;
+        const bool valid = lane < k;
+        const P p = a.sp[valid ? q : s];
+        const bool qcore = valid && a.core[q];
+        for (int u = 1; u < k; ++u) {
+            const P pu = NB<D>::shfl(p, u);
+            const bool cu = __shfl_sync(FULL, qcore, u);
+            if (lane < u && dist2(p, pu) <= a.e2) rule.pair(q, qcore, s + u, cu);
+            __syncwarp();
+        }
+        __syncwarp();
+        // minPts <= 2 marks core points while pairing: read the flags again
+        const bool c = !valid || a.core[q];
+        const int root = valid ? uf_find(a.labels, q) : -1;
+        const int root0 = __shfl_sync(FULL, root, 0);
+        const bool solid = __all_sync(FULL, c && (!valid || root == root0));
+        if (lane == 0) a.lsolid[L] = solid ? 1 : 0;
     }
 }
 
@@ -484,42 +637,48 @@ __global__ void k_main(DevArgs<D> a)
         if (L >= m) break;
         const int2 r = a.leafr[L];
         const int s = r.x, e = r.y & 0x7fffffff;
-        if (r.y >= 0) {
+        if (r.y >= 0 && a.lsolid[L]) {
+            MainSolidV<D> v;
+            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
+            v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
+            v.valid = s + lane < e;
+            v.p = a.sp[v.valid ? s + lane : s];
+            v.qb.lo = a.nodebox[(m - 1) + L].lo;
+            v.qb.hi = a.nodebox[(m - 1) + L].hi;
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+        } else if (!a.lsolid[L]) {
             MainPtV<D> v;
-            v.sp = a.sp; v.leafr = a.leafr; v.core = a.core; v.buf = wm->buf; v.cbuf = wm->cbuf;
-            v.rule = rule; v.e2 = a.e2; v.mask_lo = L; v.lane = lane; v.sQ = s;
+            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
+            v.cbuf = wm->cbuf; v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
             v.q = s + lane;
             v.valid = v.q < e;
             v.p = a.sp[v.valid ? v.q : s];
             v.qcore = v.valid && a.core[v.q];
-            traverse<D>(a.nodes, m, v, wm->stack, a.ctrl);
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
         } else {
             MainBoxV<D> v;
-            v.sp = a.sp; v.leafr = a.leafr; v.core = a.core; v.buf = wm->buf;
-            v.rule = rule; v.e2 = a.e2; v.mask_lo = L; v.lane = lane; v.sQ = s; v.eQ = e;
+            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
+            v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, m, v, wm->stack, a.ctrl);
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
         }
     }
 }
 
-// labels[i] = i (or the dense cell's first point); core = 1 in dense cells
-// (and everywhere when minPts == 1)
-__global__ void k_init(const int2* __restrict__ leafr, const uint32_t* __restrict__ ctrl, int min_pts,
-                       int32_t* __restrict__ labels, uint8_t* __restrict__ core)
+// labels[i] = i, or the first point of its dense cell (pre-united, Sec. 4.2);
+// core = 1 in dense cells (and everywhere when minPts == 1)
+__global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __restrict__ cellid,
+                       const int32_t* __restrict__ cstart, int64_t n, int min_pts, int32_t* __restrict__ labels,
+                       uint8_t* __restrict__ core)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t m = ctrl[CTRL_M];
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t l = wid; l < m; l += nw) {
-        const int2 r = leafr[l];
-        const int s = r.x, e = r.y & 0x7fffffff;
-        const bool dense = r.y < 0;
-        for (int j = s + lane; j < e; j += 32) {
-            labels[j] = dense ? s : j;
-            core[j] = (dense || min_pts == 1) ? 1 : 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (pdense && pdense[i]) {
+            labels[i] = cstart[cellid[i] - 1];
+            core[i] = 1;
+        } else {
+            labels[i] = (int32_t)i;
+            core[i] = min_pts == 1 ? 1 : 0;
         }
     }
 }
@@ -573,6 +732,7 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.nodes = static_cast<const typename Traits<D>::Node*>(a.nodes);
     d.nodebox = static_cast<const typename Traits<D>::Box*>(a.nodebox);
     d.leafr = a.leafr;
+    d.lsolid = a.lsolid;
     d.labels = a.labels;
     d.core = a.core;
     d.ctrl = a.ctrl;
@@ -593,6 +753,9 @@ void run_pre(const ClusterArgs& a, cudaStream_t s)
 template <int D>
 void run_main(const ClusterArgs& a, cudaStream_t s)
 {
+    int64_t gw = (a.m_cap * 32 + 255) / 256;
+    if (gw > 152 * 16) gw = 152 * 16;
+    k_intra<D><<<(unsigned)gw, 256, 0, s>>>(dev_args<D>(a));
     const size_t smem = sizeof(WarpMem<D>) * (size_t)(a.block / 32);
     const int g = persistent_blocks<D>((const void*)k_main<D>, a.block, smem);
     k_main<D><<<g, a.block, smem, s>>>(dev_args<D>(a));
@@ -604,9 +767,9 @@ cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-    int64_t gw = (a.m_cap * 32 + 255) / 256;
-    if (gw > 152 * 16) gw = 152 * 16;
-    k_init<<<(unsigned)gw, 256, 0, s>>>(a.leafr, a.ctrl, a.min_pts, a.labels, a.core);
+    int64_t gn = (a.n + 255) / 256;
+    if (gn > 152 * 16) gn = 152 * 16;
+    k_init<<<(unsigned)gn, 256, 0, s>>>(a.pdense, a.cellid, a.cstart, a.n, a.min_pts, a.labels, a.core);
     note_launches(1);
     if ((e = cudaMemsetAsync(a.canon, 0x7f, sizeof(int32_t) * (size_t)a.n, s)) != cudaSuccess) return e;
     return cudaGetLastError();
@@ -623,7 +786,7 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
 {
     if (a.dim == 3) run_main<3>(a, s); else run_main<2>(a, s);
-    note_launches(1);
+    note_launches(2);
     return cudaGetLastError();
 }
 
