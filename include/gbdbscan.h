@@ -187,7 +187,7 @@ const char* dbscan_profile_stage_name(int stage);
 int64_t dbscan_kernel_launches(void);
 
 /* Statistics of the last dbscan_run on `stream` (waits for it):
- * stats_out[0] = number of BVH leaves m, stats_out[1] = number of grid cells
+ * stats_out[0] = number of BVH leaves m, stats_out[1] = number of dense cells
  * (DenseBox; 0 for FDBSCAN). */
 dbscan_status dbscan_last_stats(dbscan_stream stream, int64_t* stats_out);
 

@@ -315,10 +315,10 @@ def kernel_launches() -> int:
 
 
 def last_stats(stream=None) -> dict:
-    """Statistics of the last run on the stream: BVH leaves m, grid cells."""
+    """Statistics of the last run on the stream: BVH leaves m, dense cells."""
     out = (ctypes.c_int64 * 2)()
     _check(load().dbscan_last_stats(_stream_handle(stream), out))
-    return {"leaves": int(out[0]), "cells": int(out[1])}
+    return {"leaves": int(out[0]), "dense_cells": int(out[1])}
 
 
 def set_tuning(block_size: int = 0, cell_factor: float = 0.0):

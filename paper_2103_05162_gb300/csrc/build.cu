@@ -170,61 +170,57 @@ __global__ void k_gather(const float* __restrict__ pts, const uint32_t* __restri
 // "all points core and in one cluster" (Sec. 4.2) holds exactly, whatever
 // rounding the grid arithmetic suffered (the precision hazard of Sec. 4.2 is
 // turned into a per-cell check instead of an abort).
+//
+// One pass: the thread at the first point of a run checks with one load
+// whether the run reaches minPts points; only those runs are then walked, by
+// the whole warp, for the box and the guard, and their points marked 1
+// (dense, fits in a tile) or 2 (dense, larger than a tile: a leaf of its
+// own), with the run's first point. pdense must be zero on entry.
 // ---------------------------------------------------------------------------
-__global__ void k_cell_heads(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ head)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
-}
-
-// cellid = inclusive scan of head (1-based); writes cell starts and count
-__global__ void k_cell_starts(const int32_t* __restrict__ head, const int32_t* __restrict__ cellid, int64_t n,
-                              int32_t* __restrict__ cstart, uint32_t* __restrict__ ctrl)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (head[i]) cstart[cellid[i] - 1] = (int32_t)i;
-        if (i == n - 1) {
-            cstart[cellid[i]] = (int32_t)n;
-            ctrl[CTRL_NCELLS] = (uint32_t)cellid[i];
-        }
-    }
-}
-
-// one warp per candidate cell (count >= minPts): exact box and the guard
 template <int D>
-__global__ void k_cell_dense(const typename Traits<D>::Point* __restrict__ sp, const int32_t* __restrict__ cstart,
-                             const uint32_t* __restrict__ ctrl, int min_pts, float e2, uint8_t* __restrict__ cdense)
+__global__ void k_dense_classify(const uint64_t* __restrict__ keys, const typename Traits<D>::Point* __restrict__ sp,
+                                 int64_t n, int min_pts, float e2, uint8_t* __restrict__ pdense,
+                                 int32_t* __restrict__ dstart, uint32_t* __restrict__ ctrl)
 {
     using T = Traits<D>;
     const int lane = threadIdx.x & 31;
-    const int64_t ncells = ctrl[CTRL_NCELLS];
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = wid; c < ncells; c += nw) {
-        const int s = cstart[c], e = cstart[c + 1];
-        if (e - s < min_pts) {
-            if (lane == 0) cdense[c] = 0;
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together so that the cell walks below are cooperative
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; base < n; base += stride) {
+        const int64_t i = base + lane;
+        bool cand = false;
+        if (i < n) {
+            const uint64_t k = keys[i];
+            const int64_t j = i + min_pts - 1;
+            cand = (i == 0 || keys[i - 1] != k) && j < n && keys[j] == k;
         }
-        typename T::Box b = T::empty_box();
-        for (int j = s + lane; j < e; j += 32) T::grow(b, sp[j]);
+        unsigned cm = __ballot_sync(FULL, cand);
+        while (cm) {
+            const int src = __ffs(cm) - 1;
+            cm &= cm - 1;
+            const int64_t c0 = __shfl_sync(FULL, i, src);
+            const uint64_t k = keys[c0];
+            // walk the run with the whole warp: extent and exact box
+            typename T::Box b = T::empty_box();
+            int64_t e = c0;
+            for (;;) {
+                const int64_t t = e + lane;
+                const bool in = t < n && keys[t] == k;
+                if (in) T::grow(b, sp[t]);
+                const unsigned im = __ballot_sync(FULL, in);
+                e += __popc(im);
+                if (im != FULL) break;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
-        if (lane == 0) cdense[c] = T::diag2(b) <= e2 ? 1 : 0;
-    }
-}
-
-// per point: 0 outside dense cells, 1 in a dense cell that fits in a tile
-// (at most TILE points: it stays inside a tile, pre-united and core), 2 in a
-// larger dense cell (one BVH leaf of its own, queried as a box)
-__global__ void k_point_flags(const int32_t* __restrict__ cellid, const int32_t* __restrict__ cstart,
-                              const uint8_t* __restrict__ cdense, int64_t n, uint8_t* __restrict__ pdense)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = cellid[i] - 1;
-        uint8_t f = 0;
-        if (cdense[c]) f = (cstart[c + 1] - cstart[c] > TILE) ? 2 : 1;
-        pdense[i] = f;
+            for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
+            if (T::diag2(b) > e2) continue;  // the guard: not provably one clique
+            const uint8_t f = (e - c0 > TILE) ? 2 : 1;
+            for (int64_t t = c0 + lane; t < e; t += 32) {
+                pdense[t] = f;
+                dstart[t] = (int32_t)c0;
+            }
+            if (lane == 0) atomicAdd(&ctrl[CTRL_NCELLS], 1u);
+        }
     }
 }
 
@@ -270,13 +266,13 @@ __device__ __forceinline__ bool radix_split_exceeds(const K* __restrict__ k, int
 // subtrees of at most T points (spatially compact, unlike fixed runs of T in
 // Morton order, which can straddle a jump of the curve).
 template <typename K>
-__global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ head,
+__global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ dstart,
                              const uint8_t* __restrict__ pdense, int64_t n, int T, int32_t* __restrict__ lf)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int f;
         if (i == 0) f = 1;
-        else if (pdense && pdense[i] == 2) f = head[i];
+        else if (pdense && pdense[i] == 2) f = dstart[i] == (int32_t)i ? 1 : 0;
         else if (pdense && pdense[i - 1] == 2) f = 1;
         else f = radix_split_exceeds(keys, n, i - 1, T) ? 1 : 0;
         lf[i] = f;
@@ -483,20 +479,19 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_cell_heads<<<g, 256, 0, s>>>(keys, n, t.head);
-    if ((e = scan_i32(t.head, t.cellid, n, SCAN_ADD, true, t.scan_temp, s)) != cudaSuccess) return e;
-    k_cell_starts<<<g, 256, 0, s>>>(t.head, t.cellid, n, t.cstart, ctrl);
-    const unsigned gw = 152 * 16;  // warps stride over cells
+    if ((e = cudaMemsetAsync(t.pdense, 0, (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctrl + CTRL_NCELLS, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     if (dim == 3)
-        k_cell_dense<3><<<gw, 256, 0, s>>>(static_cast<const float4*>(sp), t.cstart, ctrl, min_pts, e2, t.cdense);
+        k_dense_classify<3><<<g, 256, 0, s>>>(keys, static_cast<const float4*>(sp), n, min_pts, e2, t.pdense,
+                                              t.dstart, ctrl);
     else
-        k_cell_dense<2><<<gw, 256, 0, s>>>(static_cast<const float2*>(sp), t.cstart, ctrl, min_pts, e2, t.cdense);
-    k_point_flags<<<g, 256, 0, s>>>(t.cellid, t.cstart, t.cdense, n, t.pdense);
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.head, t.pdense, n, TILE, t.lf);
+        k_dense_classify<2><<<g, 256, 0, s>>>(keys, static_cast<const float2*>(sp), n, min_pts, e2, t.pdense,
+                                              t.dstart, ctrl);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, t.lf);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, leafr, lkey);
-    note_launches(7);
+    note_launches(4);
     return cudaGetLastError();
 }
 

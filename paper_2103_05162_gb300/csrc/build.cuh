@@ -14,10 +14,13 @@ enum : int {
     CTRL_NONFINITE = 8,  // nonzero if a coordinate is NaN/Inf
     CTRL_ERR = 9,        // device error bits (ERR_*)
     CTRL_M = 10,         // number of BVH leaves
-    CTRL_NCELLS = 11,    // number of grid cells (DenseBox)
+    CTRL_NCELLS = 11,    // number of dense cells (DenseBox)
     CTRL_WORK_PRE = 12,  // work counters of the persistent traversal kernels
     CTRL_WORK_MAIN = 13,
-    CTRL_WORDS = 16
+    CTRL_KIND_COUNT = 16,  // 3 words: leaves per kind (0 tile, 1 solid tile, 2 dense cell leaf)
+    CTRL_KIND_FILL = 19,   // 3 words: fill counters of the per-kind leaf lists
+    CTRL_KIND_WORK = 22,   // 3 words: work counters of the per-kind main kernels
+    CTRL_WORDS = 32
 };
 
 constexpr unsigned ERR_STACK = 2u;  // traversal/refit limits exceeded (cannot happen for valid trees)
@@ -32,11 +35,8 @@ struct GridParams {
 };
 
 struct DenseBoxTemps {
-    int32_t* head;      // n
-    int32_t* cellid;    // n
-    int32_t* cstart;    // n + 1
-    uint8_t* cdense;    // n
     uint8_t* pdense;    // n: 0 not dense, 1 dense cell within a tile, 2 dense cell as its own leaf
+    int32_t* dstart;    // n: first point of the dense cell (valid where pdense != 0)
     int32_t* lf;        // n
     int32_t* lidx;      // n
     int32_t* lstart;    // n + 1
@@ -68,12 +68,13 @@ struct ClusterArgs {
     const void* nodebox;   // 2m-1 boxes (leaf boxes at m-1+l)
     const int2* leafr;     // m leaf records
     uint8_t* lsolid;       // m: 1 if all points of the leaf are core and in one set
+    int32_t* klist;        // m: leaf indices grouped by kind
     const uint8_t* pdense; // n or null: dense-cell flags per sorted point (DenseBox)
-    const int32_t* cellid; // n or null: 1-based cell of each sorted point
-    const int32_t* cstart; // cells + 1 or null: first point of each cell
+    const int32_t* dstart; // n or null: first point of each point's dense cell
     const uint32_t* perm;  // sorted position -> input index
     int32_t* labels;       // n (union-find parents, sorted index space)
     uint8_t* core;         // n (sorted order)
+    uint8_t* nbr;          // n: 1 if another point is within eps (set by preprocessing)
     int32_t* canon;        // n (smallest input index per root)
     uint32_t* ctrl;
     int64_t n;

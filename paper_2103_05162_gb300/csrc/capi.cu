@@ -44,7 +44,7 @@ dbscan_status cuda_error(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_error(e_, #x);   \
     } while (0)
 
-Tuning g_tuning = {256, 1.0f};
+Tuning g_tuning = {128, 1.0f};
 
 // ---------------------------------------------------------------------------
 // launch counting and opt-in per-stage timing (CUDA events on the stream)
@@ -136,8 +136,10 @@ struct Plan {
     int32_t* parent;
     int32_t* visit;
     uint8_t* lsolid;
+    int32_t* klist;
     int32_t* labels;
     uint8_t* core;
+    uint8_t* nbr;
     int32_t* canon;
 };
 
@@ -164,11 +166,8 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
     p.status = c.take<uint32_t>(sort_status_words(n, 8, 64));
     p.sp = c.take<char>(pt * (size_t)n);
     if (algo == DBSCAN_ALGO_DENSEBOX) {
-        p.db.head = c.take<int32_t>(n);
-        p.db.cellid = c.take<int32_t>(n);
-        p.db.cstart = c.take<int32_t>(n + 1);
-        p.db.cdense = c.take<uint8_t>(n);
         p.db.pdense = c.take<uint8_t>(n);
+        p.db.dstart = c.take<int32_t>(n);
     } else {
         p.db = DenseBoxTemps{};
     }
@@ -184,8 +183,10 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
     p.parent = c.take<int32_t>(2 * mc);
     p.visit = c.take<int32_t>(mc);
     p.lsolid = c.take<uint8_t>(mc);
+    p.klist = c.take<int32_t>(mc);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
+    p.nbr = c.take<uint8_t>(n);
     p.canon = c.take<int32_t>(n);
     return c.off + 256;
 }
@@ -339,6 +340,7 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     // K1 bounds, then one host wait for them
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, 4 * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, 5 * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_M, 0, 2 * sizeof(uint32_t), s));
     T.begin(ST_BOUNDS);
     launch_bounds(points, n, dim, p.ctrl, s);
     T.end();
@@ -418,12 +420,13 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     a.nodebox = p.nodebox;
     a.leafr = p.leafr;
     a.lsolid = p.lsolid;
+    a.klist = p.klist;
     a.pdense = algo == DBSCAN_ALGO_DENSEBOX ? p.db.pdense : nullptr;
-    a.cellid = algo == DBSCAN_ALGO_DENSEBOX ? p.db.cellid : nullptr;
-    a.cstart = algo == DBSCAN_ALGO_DENSEBOX ? p.db.cstart : nullptr;
+    a.dstart = algo == DBSCAN_ALGO_DENSEBOX ? p.db.dstart : nullptr;
     a.perm = perm;
     a.labels = p.labels;
     a.core = p.core;
+    a.nbr = p.nbr;
     a.canon = p.canon;
     a.ctrl = p.ctrl;
     a.n = n;
@@ -620,7 +623,7 @@ dbscan_status dbscan_set_tuning(int block_size, float cell_factor)
         return set_error(DBSCAN_ERR_INVALID_ARG, "block size must be a multiple of 32 in [32, 1024]");
     if (cell_factor != 0.0f && !(cell_factor > 0.0f && cell_factor <= 1.0f))
         return set_error(DBSCAN_ERR_INVALID_ARG, "cell factor must be in (0, 1]");
-    g_tuning.block = block_size ? block_size : 256;
+    g_tuning.block = block_size ? block_size : 128;
     g_tuning.cell_factor = cell_factor != 0.0f ? cell_factor : 1.0f;
     return DBSCAN_OK;
 }

@@ -11,6 +11,7 @@ namespace gbd {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TILE = 32;  // points per non-dense BVH leaf (one warp lane per point)
+constexpr int SORT_TILE_KEYS = 256 * 16;  // keys per look-back tile of the radix sort (256 threads x 16)
 
 // bits of the device error word
 constexpr unsigned ERR_SORT_TIMEOUT = 1u;

@@ -26,7 +26,7 @@ namespace gbd {
 namespace {
 
 constexpr int64_t NOALLOC_MAX_PAIRS = DBSCAN_SORT_NOALLOC_MAX_PAIRS;
-constexpr int64_t NOALLOC_TILE_KEYS = 4096;  // keys per look-back tile of the onesweep kernel
+constexpr int64_t NOALLOC_TILE_KEYS = SORT_TILE_KEYS;  // keys per look-back tile of the onesweep kernel
 constexpr int64_t NOALLOC_TILES = (NOALLOC_MAX_PAIRS + NOALLOC_TILE_KEYS - 1) / NOALLOC_TILE_KEYS;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }

@@ -20,8 +20,9 @@ namespace {
 constexpr int THREADS = 256;  // == radix: thread t owns digit t in the per-digit steps
 constexpr int WARPS = THREADS / 32;
 constexpr int RADIX = 256;
-constexpr int ITEMS = 16;
+constexpr int ITEMS = 16;  // keys per thread (8 was measured slower despite 3 blocks per SM)
 constexpr int TILE_ITEMS = THREADS * ITEMS;
+static_assert(TILE_ITEMS == SORT_TILE_KEYS, "tile size shared with the static-scratch entry point");
 constexpr uint32_t FLAG_AGG = 1u << 30;
 constexpr uint32_t FLAG_PRE = 2u << 30;
 constexpr uint32_t VAL_MASK = (1u << 30) - 1;

@@ -151,24 +151,23 @@ __device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restr
         if (nd.m.z >= v.mask_lo) ml = __ballot_sync(FULL, v.hit_l(nd));
         if (nd.m.w >= v.mask_lo) mr = __ballot_sync(FULL, v.hit_r(nd));
         int next = -1;
-        if (ml) {
-            if (nd.m.x >= leaf0) {
-                if (v.leaf(nd.m.x - leaf0, ml, NB<D>::box_l(nd))) return;
-            } else {
-                next = nd.m.x;
-            }
-        }
-        if (mr) {
-            if (nd.m.y >= leaf0) {
-                if (v.leaf(nd.m.y - leaf0, mr, NB<D>::box_r(nd))) return;
+        // left child, then right child; one call site of v.leaf keeps the
+        // kernel's code small
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            const unsigned mk = c ? mr : ml;
+            if (!mk) continue;
+            const int child = c ? nd.m.y : nd.m.x;
+            if (child >= leaf0) {
+                if (v.leaf(child - leaf0, mk, c ? NB<D>::box_r(nd) : NB<D>::box_l(nd))) return;
             } else if (next < 0) {
-                next = nd.m.y;
+                next = child;
             } else {
                 if (sp >= STACK) {
                     if (lane == 0) atomicOr(&ctrl[CTRL_ERR], ERR_STACK);
                     return;
                 }
-                if (lane == 0) stack[sp] = nd.m.y;
+                if (lane == 0) stack[sp] = child;
                 ++sp;
             }
         }
@@ -194,6 +193,7 @@ struct PreV {
     float e2;
     int min_pts;
     int mask_lo;
+    int own;  // the query tile's own leaf, already counted
     int lane;
     P p;
     bool act;
@@ -205,6 +205,7 @@ struct PreV {
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
     {
+        if (L == own) return false;
         const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
         mask &= __ballot_sync(FULL, act);
@@ -266,6 +267,23 @@ struct Rule {
         if (__ldcg(labels + a) == __ldcg(labels + b)) return;  // same parent: same set
         uf_union(labels, a, b);
     }
+    // pair() with a per-lane memo of the last core partner's parent: a
+    // partner with the same parent is in a set already united with a (sets
+    // never split), so the union is skipped. Partners come in sorted order and
+    // mostly share an intra-tile root, so most unions are skipped this way.
+    __device__ __forceinline__ void pair_memo(int a, bool acore, int b, bool bcore, int& last) const
+    {
+        if (min_pts <= 2 || (acore && bcore)) {
+            if (min_pts == 2) { core[a] = 1; core[b] = 1; }
+            const int lb = __ldcg(labels + b);
+            if (lb == last) return;
+            unite(a, b);
+            last = lb;
+        } else if (mode == DBSCAN_MODE_DBSCAN) {
+            if (acore) uf_claim(labels, b, a);
+            else if (bcore) uf_claim(labels, a, b);
+        }
+    }
     __device__ __forceinline__ void pair(int a, bool acore, int b, bool bcore) const
     {
         if (min_pts <= 2) {
@@ -317,6 +335,7 @@ struct MainPtV {
     int q;
     bool valid;
     bool qcore;
+    int last = -1;  // pair_memo state of this lane's query
 
     __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return valid && NB<D>::pl(n, p) <= e2; }
     __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return valid && NB<D>::pr(n, p) <= e2; }
@@ -335,6 +354,7 @@ struct MainPtV {
                 const int ri = s + lane;
                 const P rp = in ? sp[ri] : sp[s];
                 const bool rc = in && core[ri];
+                int rlast = -1;  // pair_memo state of this lane's leaf point
                 unsigned mm = mask;
                 while (mm) {
                     const int qq = __ffs(mm) - 1;
@@ -342,7 +362,7 @@ struct MainPtV {
                     const P pq = NB<D>::shfl(p, qq);
                     const bool qc = __shfl_sync(FULL, qcore, qq);
                     const bool qcont = __shfl_sync(FULL, cont, qq);
-                    if (in && (qcont || dist2(pq, rp) <= e2)) rule.pair(sQ + qq, qc, ri, rc);
+                    if (in && (qcont || dist2(pq, rp) <= e2)) rule.pair_memo(ri, rc, sQ + qq, qc, rlast);
                     __syncwarp();
                 }
             } else {
@@ -350,7 +370,7 @@ struct MainPtV {
                 __syncwarp();
                 if ((mask >> lane) & 1u)
                     for (int u = 0; u < k; ++u)
-                        if (cont || dist2(p, buf[u]) <= e2) rule.pair(q, qcore, s + u, cbuf[u] != 0);
+                        if (cont || dist2(p, buf[u]) <= e2) rule.pair_memo(q, qcore, s + u, cbuf[u] != 0, last);
                 __syncwarp();
             }
             return false;
@@ -543,8 +563,10 @@ struct DevArgs {
     const typename Traits<D>::Box* nodebox;
     const int2* leafr;
     uint8_t* lsolid;
+    int32_t* klist;
     int32_t* labels;
     uint8_t* core;
+    uint8_t* nbr;
     uint32_t* ctrl;
     float e2;
     int min_pts;
@@ -570,24 +592,44 @@ __global__ void k_pre(DevArgs<D> a)
         if (L >= m) break;
         const int2 r = a.leafr[L];
         if (r.y < 0) continue;  // dense cell: all core already
-        const int s = r.x, e = r.y;
+        const int s = r.x, e = r.y, k = e - s;
         const int q = s + lane;
         // points of dense cells inside the tile are core already
         const bool counts = q < e && !a.core[q];
         if (!__any_sync(FULL, counts)) continue;
+        const typename Traits<D>::Point p = a.sp[q < e ? q : s];
+        // the tile's own points first: in dense regions most queries reach
+        // minPts here and need no traversal at all
+        wm->buf[lane] = p;
+        __syncwarp();
+        int cnt = 0;
+        if (counts)
+            for (int u = 0; u < k; ++u)
+                if (dist2(p, wm->buf[u]) <= a.e2 && ++cnt >= a.min_pts) break;
+        __syncwarp();
         PreV<D> v;
         v.sp = a.sp; v.leafr = a.leafr; v.buf = wm->buf; v.e2 = a.e2; v.min_pts = a.min_pts;
-        v.mask_lo = 0; v.lane = lane;
-        v.act = counts;
-        v.p = a.sp[q < e ? q : s];
-        v.cnt = 0;
-        traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
-        if (counts) a.core[q] = v.cnt >= a.min_pts ? 1 : 0;
+        v.mask_lo = 0; v.own = L; v.lane = lane;
+        v.act = counts && cnt < a.min_pts;
+        v.p = p;
+        v.cnt = cnt;
+        if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+        if (counts) {
+            a.core[q] = v.cnt >= a.min_pts ? 1 : 0;
+            a.nbr[q] = v.cnt >= 2 ? 1 : 0;  // another point within eps (the count includes q)
+        }
     }
 }
 
-// Each tile unites its own pairs (q, q') with q' > q, then records whether it
-// is solid: all its points core and in one set. Dense cells are solid.
+// Each tile resolves its own pairs (q, q') with q' > q. Every lane builds the
+// bit mask of the tile points within eps of its point; the components of the
+// core points follow from doubling reach sets (the union of the reach sets
+// of the points already reached) over warp shuffles, at most five rounds for
+// 32 points; each core point then joins its component's first point
+// globally (at most one union per point), and a non-core point with a core
+// neighbour in the tile claims it. Finally the tile records whether it is
+// solid: all points core and in one set. Dense cells larger than a tile are
+// solid by construction.
 template <int D>
 __global__ void k_intra(DevArgs<D> a)
 {
@@ -596,7 +638,6 @@ __global__ void k_intra(DevArgs<D> a)
     const int64_t m = a.ctrl[CTRL_M];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const Rule rule{a.labels, a.core, a.min_pts, a.mode};
     for (int64_t L = wid; L < m; L += nw) {
         const int2 r = a.leafr[L];
         if (r.y < 0) {
@@ -604,40 +645,126 @@ __global__ void k_intra(DevArgs<D> a)
             continue;
         }
         const int s = r.x, k = r.y - r.x;
-        const int q = s + lane;
         const bool valid = lane < k;
-        const P p = a.sp[valid ? q : s];
-        const bool qcore = valid && a.core[q];
-        for (int u = 1; u < k; ++u) {
-            const P pu = NB<D>::shfl(p, u);
-            const bool cu = __shfl_sync(FULL, qcore, u);
-            if (lane < u && dist2(p, pu) <= a.e2) rule.pair(q, qcore, s + u, cu);
-            __syncwarp();
+        const P p = a.sp[valid ? s + lane : s];
+        unsigned adj = 0;
+        for (int j = 0; j < k; ++j) {
+            const P pj = NB<D>::shfl(p, j);
+            if (valid && j != lane && dist2(p, pj) <= a.e2) adj |= 1u << j;
+        }
+        bool c = valid && a.core[s + lane];
+        if (a.min_pts == 2) {
+            // no preprocessing: a neighbour inside the tile makes a point core
+            // (neighbours in other tiles are found by the main phase)
+            c = valid && (c || adj != 0);
+            if (c) a.core[s + lane] = 1;
+        }
+        const unsigned cm = __ballot_sync(FULL, c);
+        if (a.min_pts > 2 && a.mode == DBSCAN_MODE_DBSCAN && valid && !c && (adj & cm))
+            uf_claim(a.labels, s + lane, s + __ffs(adj & cm) - 1);
+        unsigned reach = c ? ((adj & cm) | (1u << lane)) : 0u;
+        for (int it = 0; it < 5; ++it) {
+            unsigned acc = reach;
+            for (int j = 0; j < k; ++j) {
+                const unsigned rj = __shfl_sync(FULL, reach, j);
+                if ((reach >> j) & 1u) acc |= rj;
+            }
+            const bool changed = acc != reach;
+            reach = acc;
+            if (!__any_sync(FULL, changed)) break;
+        }
+        if (c) {
+            const int lr = __ffs(reach) - 1;
+            if (lr != lane) uf_union(a.labels, s + lane, s + lr);
         }
         __syncwarp();
-        // minPts <= 2 marks core points while pairing: read the flags again
-        const bool c = !valid || a.core[q];
-        const int root = valid ? uf_find(a.labels, q) : -1;
+        const int root = c ? uf_find(a.labels, s + lane) : -1;
         const int root0 = __shfl_sync(FULL, root, 0);
-        const bool solid = __all_sync(FULL, c && (!valid || root == root0));
+        const bool solid = __all_sync(FULL, !valid || (c && root == root0));
         if (lane == 0) a.lsolid[L] = solid ? 1 : 0;
+        __syncwarp();
     }
 }
 
-template <int D>
+// Leaf kinds for the main phase: 0 a tile that is not solid, 1 a solid tile,
+// 2 a dense cell larger than a tile. Lists are grouped by kind; within a warp
+// (32 consecutive leaves) the order is kept.
+__device__ __forceinline__ int leaf_kind(const int2* leafr, const uint8_t* lsolid, int64_t L)
+{
+    return leafr[L].y < 0 ? 2 : (lsolid[L] ? 1 : 0);
+}
+
+__global__ void k_kinds_count(const int2* __restrict__ leafr, const uint8_t* __restrict__ lsolid, uint32_t* ctrl)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t m = ctrl[CTRL_M];
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < m;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = base + lane;
+        const int kind = L < m ? leaf_kind(leafr, lsolid, L) : -1;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const unsigned b = __ballot_sync(FULL, kind == t);
+            if (lane == 0 && b) atomicAdd(&ctrl[CTRL_KIND_COUNT + t], (uint32_t)__popc(b));
+        }
+    }
+}
+
+__global__ void k_kinds_write(const int2* __restrict__ leafr, const uint8_t* __restrict__ lsolid, uint32_t* ctrl,
+                              int32_t* __restrict__ klist)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t m = ctrl[CTRL_M];
+    const uint32_t off[3] = {0u, ctrl[CTRL_KIND_COUNT], ctrl[CTRL_KIND_COUNT] + ctrl[CTRL_KIND_COUNT + 1]};
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < m;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = base + lane;
+        const int kind = L < m ? leaf_kind(leafr, lsolid, L) : -1;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const unsigned b = __ballot_sync(FULL, kind == t);
+            if (!b) continue;
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(&ctrl[CTRL_KIND_FILL + t], (uint32_t)__popc(b));
+            at = __shfl_sync(FULL, at, 0);
+            if (kind == t) klist[off[t] + at + __popc(b & lt)] = (int32_t)L;
+        }
+    }
+}
+
+// The main phase for the leaves of one kind (KIND 0: MainPtV, 1: MainSolidV,
+// 2: MainBoxV), taken from the kind's list through a work counter.
+template <int D, int KIND>
 __global__ void k_main(DevArgs<D> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t m = a.ctrl[CTRL_M];
-    Rule rule{a.labels, a.core, a.min_pts, a.mode};
+    uint32_t off = 0;
+    for (int t = 0; t < KIND; ++t) off += a.ctrl[CTRL_KIND_COUNT + t];
+    const int64_t cnt = a.ctrl[CTRL_KIND_COUNT + KIND];
+    const Rule rule{a.labels, a.core, a.min_pts, a.mode};
     for (;;) {
-        const int L = next_leaf(&a.ctrl[CTRL_WORK_MAIN]);
-        if (L >= m) break;
+        const int idx = next_leaf(&a.ctrl[CTRL_KIND_WORK + KIND]);
+        if (idx >= cnt) break;
+        const int L = a.klist[off + idx];
         const int2 r = a.leafr[L];
         const int s = r.x, e = r.y & 0x7fffffff;
-        if (r.y >= 0 && a.lsolid[L]) {
+        if (KIND == 0) {
+            MainPtV<D> v;
+            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
+            v.cbuf = wm->cbuf; v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
+            v.q = s + lane;
+            const bool in = v.q < e;
+            v.qcore = in && a.core[v.q];
+            // after preprocessing a non-core point with no other point within
+            // eps takes part in no pair, and in DBSCAN* no non-core point does
+            v.valid = in && (a.min_pts <= 2 || v.qcore || (a.mode == DBSCAN_MODE_DBSCAN && a.nbr[v.q]));
+            v.p = a.sp[in ? v.q : s];
+            if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+        } else if (KIND == 1) {
             MainSolidV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
             v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
@@ -645,15 +772,6 @@ __global__ void k_main(DevArgs<D> a)
             v.p = a.sp[v.valid ? s + lane : s];
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
-        } else if (!a.lsolid[L]) {
-            MainPtV<D> v;
-            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
-            v.cbuf = wm->cbuf; v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
-            v.q = s + lane;
-            v.valid = v.q < e;
-            v.p = a.sp[v.valid ? v.q : s];
-            v.qcore = v.valid && a.core[v.q];
             traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
         } else {
             MainBoxV<D> v;
@@ -668,13 +786,12 @@ __global__ void k_main(DevArgs<D> a)
 
 // labels[i] = i, or the first point of its dense cell (pre-united, Sec. 4.2);
 // core = 1 in dense cells (and everywhere when minPts == 1)
-__global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __restrict__ cellid,
-                       const int32_t* __restrict__ cstart, int64_t n, int min_pts, int32_t* __restrict__ labels,
-                       uint8_t* __restrict__ core)
+__global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __restrict__ dstart, int64_t n,
+                       int min_pts, int32_t* __restrict__ labels, uint8_t* __restrict__ core)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (pdense && pdense[i]) {
-            labels[i] = cstart[cellid[i] - 1];
+            labels[i] = dstart[i];
             core[i] = 1;
         } else {
             labels[i] = (int32_t)i;
@@ -708,20 +825,14 @@ __global__ void k_relabel(const int32_t* labels, const uint8_t* __restrict__ cor
     }
 }
 
-template <int D>
+// blocks of a persistent launch: as many as fit on all SMs at once
 int persistent_blocks(const void* kernel, int block, size_t smem)
 {
-    static int cached[2][33] = {};
-    const int which = kernel == (const void*)k_pre<D> ? 0 : 1;
-    int& c = cached[which][block / 32];
-    if (c == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem);
-        c = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
-    }
-    return c;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem);
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
 template <int D>
@@ -733,6 +844,8 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.nodebox = static_cast<const typename Traits<D>::Box*>(a.nodebox);
     d.leafr = a.leafr;
     d.lsolid = a.lsolid;
+    d.klist = a.klist;
+    d.nbr = a.nbr;
     d.labels = a.labels;
     d.core = a.core;
     d.ctrl = a.ctrl;
@@ -745,9 +858,21 @@ DevArgs<D> dev_args(const ClusterArgs& a)
 template <int D>
 void run_pre(const ClusterArgs& a, cudaStream_t s)
 {
+    static int blocks[33] = {};
     const size_t smem = sizeof(WarpMem<D>) * (size_t)(a.block / 32);
-    const int g = persistent_blocks<D>((const void*)k_pre<D>, a.block, smem);
+    int& g = blocks[a.block / 32];
+    if (!g) g = persistent_blocks((const void*)k_pre<D>, a.block, smem);
     k_pre<D><<<g, a.block, smem, s>>>(dev_args<D>(a));
+}
+
+template <int D, int KIND>
+void run_main_kind(const ClusterArgs& a, cudaStream_t s)
+{
+    static int blocks[33] = {};
+    const size_t smem = sizeof(WarpMem<D>) * (size_t)(a.block / 32);
+    int& g = blocks[a.block / 32];
+    if (!g) g = persistent_blocks((const void*)k_main<D, KIND>, a.block, smem);
+    k_main<D, KIND><<<g, a.block, smem, s>>>(dev_args<D>(a));
 }
 
 template <int D>
@@ -756,9 +881,13 @@ void run_main(const ClusterArgs& a, cudaStream_t s)
     int64_t gw = (a.m_cap * 32 + 255) / 256;
     if (gw > 152 * 16) gw = 152 * 16;
     k_intra<D><<<(unsigned)gw, 256, 0, s>>>(dev_args<D>(a));
-    const size_t smem = sizeof(WarpMem<D>) * (size_t)(a.block / 32);
-    const int g = persistent_blocks<D>((const void*)k_main<D>, a.block, smem);
-    k_main<D><<<g, a.block, smem, s>>>(dev_args<D>(a));
+    int64_t gk = (a.m_cap + 255) / 256;
+    if (gk > 152 * 8) gk = 152 * 8;
+    k_kinds_count<<<(unsigned)gk, 256, 0, s>>>(a.leafr, a.lsolid, a.ctrl);
+    k_kinds_write<<<(unsigned)gk, 256, 0, s>>>(a.leafr, a.lsolid, a.ctrl, a.klist);
+    run_main_kind<D, 2>(a, s);
+    run_main_kind<D, 1>(a, s);
+    run_main_kind<D, 0>(a, s);
 }
 
 }  // namespace
@@ -766,10 +895,12 @@ void run_main(const ClusterArgs& a, cudaStream_t s)
 cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORDS - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
+        cudaSuccess)
+        return e;
     int64_t gn = (a.n + 255) / 256;
     if (gn > 152 * 16) gn = 152 * 16;
-    k_init<<<(unsigned)gn, 256, 0, s>>>(a.pdense, a.cellid, a.cstart, a.n, a.min_pts, a.labels, a.core);
+    k_init<<<(unsigned)gn, 256, 0, s>>>(a.pdense, a.dstart, a.n, a.min_pts, a.labels, a.core);
     note_launches(1);
     if ((e = cudaMemsetAsync(a.canon, 0x7f, sizeof(int32_t) * (size_t)a.n, s)) != cudaSuccess) return e;
     return cudaGetLastError();
@@ -786,7 +917,7 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
 {
     if (a.dim == 3) run_main<3>(a, s); else run_main<2>(a, s);
-    note_launches(2);
+    note_launches(6);
     return cudaGetLastError();
 }
 
