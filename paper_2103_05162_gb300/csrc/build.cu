@@ -46,41 +46,6 @@ __global__ void __launch_bounds__(BOUNDS_THREADS) k_bounds(const float* __restri
 // ---------------------------------------------------------------------------
 // K2: keys. Bit interleaving with axis 0 in the lowest bit.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t spread2(uint64_t x)  // 32 bits -> even bits
-{
-    x &= 0xffffffffull;
-    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
-    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
-    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
-    x = (x | (x << 2)) & 0x3333333333333333ull;
-    x = (x | (x << 1)) & 0x5555555555555555ull;
-    return x;
-}
-__device__ __forceinline__ uint64_t spread3(uint64_t x)  // 21 bits -> every third bit
-{
-    x &= 0x1fffffull;
-    x = (x | (x << 32)) & 0x001f00000000ffffull;
-    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
-// floor'd cell coordinate -> index in [0, cmax] (clamped as an integer, so
-// that cmax is exact even where it is not representable in fp32)
-__device__ __forceinline__ uint32_t cell_index(float t, uint32_t cmax)
-{
-    const uint32_t c = (uint32_t)fminf(fmaxf(t, 0.0f), 4294967040.0f);
-    return c < cmax ? c : cmax;
-}
-
-template <int D>
-__device__ __forceinline__ uint64_t interleave(const uint32_t* c)
-{
-    if (D == 3) return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
-    return spread2(c[0]) | (spread2(c[1]) << 1);
-}
-
 // Morton code of each point on a 2^bits grid over the (device-side) bounds;
 // u32 keys (FDBSCAN ordering). values = input index.
 template <int D>
@@ -267,11 +232,13 @@ __device__ __forceinline__ bool radix_split_exceeds(const K* __restrict__ k, int
 // Morton order, which can straddle a jump of the curve).
 template <typename K>
 __global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ dstart,
-                             const uint8_t* __restrict__ pdense, int64_t n, int T, int32_t* __restrict__ lf)
+                             const uint8_t* __restrict__ pdense, int64_t n, int T, int id_shift,
+                             int32_t* __restrict__ lf)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int f;
         if (i == 0) f = 1;
+        else if (id_shift < 64 && (uint64_t)(keys[i] >> id_shift) != (uint64_t)(keys[i - 1] >> id_shift)) f = 1;
         else if (pdense && pdense[i] == 2) f = dstart[i] == (int32_t)i ? 1 : 0;
         else if (pdense && pdense[i - 1] == 2) f = 1;
         else f = radix_split_exceeds(keys, n, i - 1, T) ? 1 : 0;
@@ -296,8 +263,8 @@ __global__ void k_leaf_write(const int32_t* __restrict__ lf, const int32_t* __re
 // leaf records (start, end | dense << 31) and the leaf keys
 template <typename K>
 __global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t* __restrict__ pdense,
-                               const K* __restrict__ keys, const uint32_t* __restrict__ ctrl,
-                               int2* __restrict__ leafr, uint64_t* __restrict__ lkey)
+                               const K* __restrict__ keys, const uint32_t* __restrict__ ctrl, int id_shift,
+                               int2* __restrict__ leafr, uint64_t* __restrict__ lkey, int32_t* __restrict__ linst)
 {
     const int64_t m = ctrl[CTRL_M];
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
@@ -305,6 +272,7 @@ __global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t
         const uint32_t dense = (pdense && pdense[s] == 2) ? 1u : 0u;
         leafr[l] = make_int2(s, (int32_t)((uint32_t)e | (dense << 31)));
         lkey[l] = (uint64_t)keys[s];
+        if (linst) linst[l] = (int32_t)((uint64_t)keys[s] >> id_shift);
     }
 }
 
@@ -487,11 +455,27 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
     else
         k_dense_classify<2><<<g, 256, 0, s>>>(keys, static_cast<const float2*>(sp), n, min_pts, e2, t.pdense,
                                               t.dstart, ctrl);
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, t.lf);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, 64, t.lf);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, leafr, lkey);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, 64, leafr, lkey, nullptr);
     note_launches(4);
+    return cudaGetLastError();
+}
+
+// Leaves of a batch: keys carry the instance in their bits from id_shift up;
+// tiles never cross instances. pdense/dstart come from the batch's dense-cell
+// classification (null for FDBSCAN).
+cudaError_t launch_batch_leaves(const uint64_t* keys, int64_t n, int id_shift, const DenseBoxTemps& t, int2* leafr,
+                                uint64_t* lkey, int32_t* linst, uint32_t* ctrl, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    cudaError_t e;
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, id_shift, t.lf);
+    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, id_shift, leafr, lkey, linst);
+    note_launches(3);
     return cudaGetLastError();
 }
 
@@ -500,16 +484,17 @@ cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBox
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, TILE, t.lf);
+    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, TILE, 64, t.lf);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, leafr, lkey);
+    k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, 64, leafr, lkey, nullptr);
     note_launches(3);
     return cudaGetLastError();
 }
 
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
-                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s)
+                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
+                 int2* range_out)
 {
     const unsigned gw = grid_for(m_cap * 32, 256, 152 * 16);
     const unsigned g = grid_for(m_cap, 256, 152 * 16);
@@ -517,7 +502,7 @@ void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lke
                                                      static_cast<Traits<3>::Box*>(nodebox));
     else k_leaf_boxes<2><<<gw, 256, 0, s>>>(static_cast<const float2*>(sp), leafr, ctrl,
                                              static_cast<Traits<2>::Box*>(nodebox));
-    k_karras<<<g, 256, 0, s>>>(lkey, ctrl, -1, nmeta, parent, nullptr, nullptr);
+    k_karras<<<g, 256, 0, s>>>(lkey, ctrl, -1, nmeta, parent, nullptr, range_out);
     cudaMemsetAsync(visit, 0, sizeof(int32_t) * (size_t)(m_cap > 1 ? m_cap - 1 : 1), s);
     if (dim == 3) k_refit<3><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<Traits<3>::Box*>(nodebox),
                                                static_cast<Traits<3>::Node*>(nodes), visit);

@@ -43,6 +43,44 @@ struct DenseBoxTemps {
     int32_t* scan_temp; // scan_temp_words(n)
 };
 
+// ---------------------------------------------------------------------------
+// key helpers: bit interleaving with axis 0 in the lowest bit
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread2(uint64_t x)  // 32 bits -> even bits
+{
+    x &= 0xffffffffull;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+__device__ __forceinline__ uint64_t spread3(uint64_t x)  // 21 bits -> every third bit
+{
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+// floor'd cell coordinate -> index in [0, cmax] (clamped as an integer, so
+// that cmax is exact even where it is not representable in fp32)
+__device__ __forceinline__ uint32_t cell_index(float t, uint32_t cmax)
+{
+    const uint32_t c = (uint32_t)fminf(fmaxf(t, 0.0f), 4294967040.0f);
+    return c < cmax ? c : cmax;
+}
+
+template <int D>
+__device__ __forceinline__ uint64_t interleave(const uint32_t* c)
+{
+    if (D == 3) return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+    return spread2(c[0]) | (spread2(c[1]) << 1);
+}
+
 void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStream_t s);
 void launch_morton32(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint32_t* keys,
                      uint32_t* vals, cudaStream_t s);
@@ -57,7 +95,10 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
 cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBoxTemps& t, int2* leafr,
                                uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
-                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s);
+                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
+                 int2* range_out = nullptr);
+cudaError_t launch_batch_leaves(const uint64_t* keys, int64_t n, int id_shift, const DenseBoxTemps& t, int2* leafr,
+                                uint64_t* lkey, int32_t* linst, uint32_t* ctrl, cudaStream_t s);
 void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* parent, int2* child_out,
                         int2* range_out, cudaStream_t s);
 
@@ -84,6 +125,13 @@ struct ClusterArgs {
     int min_pts;
     int mode;
     int block;             // traversal block size
+    // batches of independent instances (null for a single instance): the
+    // instance of each leaf, per-instance eps^2 / minPts, and the root of
+    // each instance's subtree; min_pts then holds the largest minPts
+    const int32_t* linst = nullptr;
+    const float* e2s = nullptr;
+    const int32_t* mps = nullptr;
+    const int32_t* iroot = nullptr;
 };
 cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s);

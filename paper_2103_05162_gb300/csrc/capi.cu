@@ -267,6 +267,13 @@ void release_stream_workspace(cudaStream_t s)
 void free_workspace(Workspace* w)
 {
     cudaStreamSynchronize(w->stream);
+    release_batch_graphs(w);
+    if (w->gstream) {
+        cudaStreamSynchronize(w->gstream);
+        cudaStreamDestroy(w->gstream);
+        cudaEventDestroy(w->fork);
+        cudaEventDestroy(w->join);
+    }
     if (w->main.base) cudaFree(w->main.base);
     if (w->aux.base) cudaFree(w->aux.base);
     if (w->io.base) cudaFree(w->io.base);
@@ -520,18 +527,8 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
-    int64_t coff = 0;
-    for (int32_t b = 0; b < count; ++b) {
-        const int64_t nb = offsets[b + 1] - offsets[b];
-        if (nb > 0) {
-            dbscan_status st = run_pipeline(w, points + coff, nb, dims[b], eps[b], min_pts[b], mode, algo,
-                                            labels_out + offsets[b], core_out ? core_out + offsets[b] : nullptr, s);
-            if (st != DBSCAN_OK) return st;
-        }
-        coff += nb * dims[b];
-    }
     (void)coords;
-    return DBSCAN_OK;
+    return run_batch(w, points, offsets, dims, eps, min_pts, count, mode, algo, labels_out, core_out, s);
 }
 
 dbscan_status dbscan_stream_status(dbscan_stream stream)

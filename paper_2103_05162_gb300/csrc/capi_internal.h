@@ -24,6 +24,10 @@ struct Workspace {
     Arena main, aux, io;
     uint32_t* ctrl_host = nullptr;  // pinned mirror of the control block
     ProfState* prof = nullptr;      // per-stage event records (profiling on)
+    // batches: the stream their CUDA graph runs on, and the events that fork
+    // it from and join it back to the caller's stream
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 struct Tuning {
@@ -43,5 +47,9 @@ void release_stream_workspace(cudaStream_t s);
 size_t workspace_bytes(int64_t n, int dim, int algo);
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
                            int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offsets, const int32_t* dims,
+                        const float* eps, const int32_t* min_pts, int32_t count, int mode, int algo,
+                        int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+void release_batch_graphs(Workspace* w);
 
 }  // namespace gbd

@@ -126,18 +126,19 @@ struct WarpMem {
 template <int D, class V>
 __device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes,
                                          const typename Traits<D>::Box* __restrict__ nodebox, int64_t m, V& v,
-                                         int* stack, uint32_t* ctrl)
+                                         int* stack, uint32_t* ctrl, int start)
 {
     const int lane = threadIdx.x & 31;
-    if (m == 1) {
+    const int leaf0 = (int)(m - 1);
+    if (start >= leaf0) {
+        // the (sub)tree is a single leaf
         typename Traits<D>::Box b;
-        b.lo = nodebox[0].lo;
-        b.hi = nodebox[0].hi;
-        v.leaf(0, v.root_mask(), b);
+        b.lo = nodebox[start].lo;
+        b.hi = nodebox[start].hi;
+        v.leaf(start - leaf0, v.root_mask(), b);
         return;
     }
-    const int leaf0 = (int)(m - 1);
-    int node = 0, sp = 0;
+    int node = start, sp = 0;
     // a traversal enters each internal node at most once; more steps than
     // that can only come from a corrupt tree: flag it and stop
     int64_t steps = 0;
@@ -279,19 +280,6 @@ struct Rule {
             if (lb == last) return;
             unite(a, b);
             last = lb;
-        } else if (mode == DBSCAN_MODE_DBSCAN) {
-            if (acore) uf_claim(labels, b, a);
-            else if (bcore) uf_claim(labels, a, b);
-        }
-    }
-    __device__ __forceinline__ void pair(int a, bool acore, int b, bool bcore) const
-    {
-        if (min_pts <= 2) {
-            // no preprocessing: any pair makes both points core (Sec. 3.2)
-            if (min_pts == 2) { core[a] = 1; core[b] = 1; }
-            unite(a, b);
-        } else if (acore && bcore) {
-            unite(a, b);
         } else if (mode == DBSCAN_MODE_DBSCAN) {
             if (acore) uf_claim(labels, b, a);
             else if (bcore) uf_claim(labels, a, b);
@@ -571,7 +559,27 @@ struct DevArgs {
     float e2;
     int min_pts;
     int mode;
+    // batches of independent instances: per-leaf instance and per-instance
+    // eps^2, minPts and subtree root (all null for a single instance)
+    const int32_t* linst;
+    const float* e2s;
+    const int32_t* mps;
+    const int32_t* iroot;
 };
+
+// eps^2, minPts and the traversal start of the tile's instance
+struct TileParams {
+    float e2;
+    int min_pts;
+    int start;
+};
+template <int D>
+__device__ __forceinline__ TileParams tile_params(const DevArgs<D>& a, int L)
+{
+    if (!a.linst) return TileParams{a.e2, a.min_pts, 0};
+    const int b = a.linst[L];
+    return TileParams{a.e2s[b], a.mps[b], a.iroot[b]};
+}
 
 __device__ __forceinline__ int next_leaf(uint32_t* ctr)
 {
@@ -592,6 +600,8 @@ __global__ void k_pre(DevArgs<D> a)
         if (L >= m) break;
         const int2 r = a.leafr[L];
         if (r.y < 0) continue;  // dense cell: all core already
+        const TileParams tp = tile_params(a, L);
+        if (tp.min_pts <= 2) continue;  // Algorithm 3: no preprocessing for minPts <= 2
         const int s = r.x, e = r.y, k = e - s;
         const int q = s + lane;
         // points of dense cells inside the tile are core already
@@ -605,17 +615,17 @@ __global__ void k_pre(DevArgs<D> a)
         int cnt = 0;
         if (counts)
             for (int u = 0; u < k; ++u)
-                if (dist2(p, wm->buf[u]) <= a.e2 && ++cnt >= a.min_pts) break;
+                if (dist2(p, wm->buf[u]) <= tp.e2 && ++cnt >= tp.min_pts) break;
         __syncwarp();
         PreV<D> v;
-        v.sp = a.sp; v.leafr = a.leafr; v.buf = wm->buf; v.e2 = a.e2; v.min_pts = a.min_pts;
+        v.sp = a.sp; v.leafr = a.leafr; v.buf = wm->buf; v.e2 = tp.e2; v.min_pts = tp.min_pts;
         v.mask_lo = 0; v.own = L; v.lane = lane;
-        v.act = counts && cnt < a.min_pts;
+        v.act = counts && cnt < tp.min_pts;
         v.p = p;
         v.cnt = cnt;
-        if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+        if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
         if (counts) {
-            a.core[q] = v.cnt >= a.min_pts ? 1 : 0;
+            a.core[q] = v.cnt >= tp.min_pts ? 1 : 0;
             a.nbr[q] = v.cnt >= 2 ? 1 : 0;  // another point within eps (the count includes q)
         }
     }
@@ -645,22 +655,23 @@ __global__ void k_intra(DevArgs<D> a)
             continue;
         }
         const int s = r.x, k = r.y - r.x;
+        const TileParams tp = tile_params(a, (int)L);
         const bool valid = lane < k;
         const P p = a.sp[valid ? s + lane : s];
         unsigned adj = 0;
         for (int j = 0; j < k; ++j) {
             const P pj = NB<D>::shfl(p, j);
-            if (valid && j != lane && dist2(p, pj) <= a.e2) adj |= 1u << j;
+            if (valid && j != lane && dist2(p, pj) <= tp.e2) adj |= 1u << j;
         }
         bool c = valid && a.core[s + lane];
-        if (a.min_pts == 2) {
+        if (tp.min_pts == 2) {
             // no preprocessing: a neighbour inside the tile makes a point core
             // (neighbours in other tiles are found by the main phase)
             c = valid && (c || adj != 0);
             if (c) a.core[s + lane] = 1;
         }
         const unsigned cm = __ballot_sync(FULL, c);
-        if (a.min_pts > 2 && a.mode == DBSCAN_MODE_DBSCAN && valid && !c && (adj & cm))
+        if (tp.min_pts > 2 && a.mode == DBSCAN_MODE_DBSCAN && valid && !c && (adj & cm))
             uf_claim(a.labels, s + lane, s + __ffs(adj & cm) - 1);
         unsigned reach = c ? ((adj & cm) | (1u << lane)) : 0u;
         for (int it = 0; it < 5; ++it) {
@@ -745,41 +756,42 @@ __global__ void k_main(DevArgs<D> a)
     uint32_t off = 0;
     for (int t = 0; t < KIND; ++t) off += a.ctrl[CTRL_KIND_COUNT + t];
     const int64_t cnt = a.ctrl[CTRL_KIND_COUNT + KIND];
-    const Rule rule{a.labels, a.core, a.min_pts, a.mode};
     for (;;) {
         const int idx = next_leaf(&a.ctrl[CTRL_KIND_WORK + KIND]);
         if (idx >= cnt) break;
         const int L = a.klist[off + idx];
+        const TileParams tp = tile_params(a, L);
+        const Rule rule{a.labels, a.core, tp.min_pts, a.mode};
         const int2 r = a.leafr[L];
         const int s = r.x, e = r.y & 0x7fffffff;
         if (KIND == 0) {
             MainPtV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
-            v.cbuf = wm->cbuf; v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
+            v.cbuf = wm->cbuf; v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
             v.q = s + lane;
             const bool in = v.q < e;
             v.qcore = in && a.core[v.q];
             // after preprocessing a non-core point with no other point within
             // eps takes part in no pair, and in DBSCAN* no non-core point does
-            v.valid = in && (a.min_pts <= 2 || v.qcore || (a.mode == DBSCAN_MODE_DBSCAN && a.nbr[v.q]));
+            v.valid = in && (tp.min_pts <= 2 || v.qcore || (a.mode == DBSCAN_MODE_DBSCAN && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
-            if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+            if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
         } else if (KIND == 1) {
             MainSolidV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
-            v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
+            v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
             v.valid = s + lane < e;
             v.p = a.sp[v.valid ? s + lane : s];
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
         } else {
             MainBoxV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
-            v.rule = rule; v.e2 = a.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
+            v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl);
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
         }
     }
 }
@@ -852,6 +864,10 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.e2 = a.e2;
     d.min_pts = a.min_pts;
     d.mode = a.mode;
+    d.linst = a.linst;
+    d.e2s = a.e2s;
+    d.mps = a.mps;
+    d.iroot = a.iroot;
     return d;
 }
 
