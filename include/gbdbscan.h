@@ -132,6 +132,23 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
  *   dbscan_server_wait     blocks until the job is done.
  *   dbscan_server_release  forgets a finished job (frees its id).
  *   dbscan_server_destroy  drains all jobs, then frees everything.
+ *   dbscan_server_set_batching  continuous batching: a slot that takes a job
+ *                          of at most max_job_points points also takes the
+ *                          later queued jobs of at most that size with the
+ *                          same mode and algo, up to max_batch_points points
+ *                          and max_batch_jobs jobs, and runs them as one
+ *                          fused batch (as dbscan_run_batch; results are the
+ *                          same as running each job alone). max_job_points
+ *                          = 0 turns it off. Defaults: 2^18, 2^24, 4096.
+ *                          Returns DBSCAN_ERR_INVALID_ARG unless
+ *                          0 <= max_job_points <= max_batch_points < 2^31
+ *                          and 1 <= max_batch_jobs <= 2^20.
+ *   dbscan_server_hold     hold != 0 pauses admission (queued jobs wait;
+ *                          running ones finish), 0 resumes it. Destroy
+ *                          resumes it before draining.
+ *   dbscan_server_stats    out4[0..3] = jobs completed, jobs run alone,
+ *                          fused batches run, jobs run inside them.
+ * The paper's method has no serving layer; this is the framework's.
  */
 typedef struct dbscan_server dbscan_server;
 dbscan_status dbscan_server_create(size_t hbm_budget_bytes, int max_slots, dbscan_server** out);
@@ -142,6 +159,10 @@ dbscan_status dbscan_server_poll(dbscan_server* srv, uint64_t job_id, int* done_
 dbscan_status dbscan_server_wait(dbscan_server* srv, uint64_t job_id);
 dbscan_status dbscan_server_release(dbscan_server* srv, uint64_t job_id);
 dbscan_status dbscan_server_destroy(dbscan_server* srv);
+dbscan_status dbscan_server_set_batching(dbscan_server* srv, int64_t max_job_points, int64_t max_batch_points,
+                                         int max_batch_jobs);
+dbscan_status dbscan_server_hold(dbscan_server* srv, int hold);
+dbscan_status dbscan_server_stats(dbscan_server* srv, int64_t* out4);
 
 /* Status of the last work enqueued by this library on `stream`: waits for the
  * stream, then returns DBSCAN_ERR_DEVICE_TIMEOUT if a bounded device-side

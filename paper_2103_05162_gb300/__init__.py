@@ -76,6 +76,9 @@ def load(build_if_missing: bool = True):
             "dbscan_server_wait": [vp, u64],
             "dbscan_server_release": [vp, u64],
             "dbscan_server_destroy": [vp],
+            "dbscan_server_set_batching": [vp, i64, i64, i32],
+            "dbscan_server_stats": [vp, vp],
+            "dbscan_server_hold": [vp, i32],
             "dbscan_stream_status": [vp],
             "dbscan_release_workspaces": [],
             "dbscan_set_tuning": [i32, f32],
@@ -219,14 +222,40 @@ class Server:
         self._keep[jid.value] = (points, labels_out, core_out)
         return jid.value
 
+    def set_batching(self, max_job_points: int = 1 << 18, max_batch_points: int = 1 << 24,
+                     max_batch_jobs: int = 4096):
+        """Continuous batching limits (max_job_points=0 turns it off)."""
+        _check(_lib.dbscan_server_set_batching(self._h, int(max_job_points), int(max_batch_points),
+                                               int(max_batch_jobs)))
+
+    def hold(self, on: bool = True):
+        """Pauses (True) or resumes (False) admission of queued jobs."""
+        _check(_lib.dbscan_server_hold(self._h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        _check(_lib.dbscan_server_stats(self._h, out))
+        return {"done": out[0], "single": out[1], "batches": out[2], "batched_jobs": out[3]}
+
     def poll(self, job_id: int):
         done = ctypes.c_int()
         lat = ctypes.c_double()
         _check(_lib.dbscan_server_poll(self._h, job_id, ctypes.byref(done), ctypes.byref(lat)))
         return bool(done.value), lat.value
 
-    def wait(self, job_id: int):
-        _check(_lib.dbscan_server_wait(self._h, job_id))
+    def wait(self, job_id: int, timeout: float | None = None):
+        """Blocks until the job is done (at most ``timeout`` seconds, then
+        TimeoutError) and returns its labels; raises DbscanError if it
+        failed."""
+        if timeout is None:
+            _check(_lib.dbscan_server_wait(self._h, job_id))
+        else:
+            import time
+            deadline = time.monotonic() + timeout
+            while not self.poll(job_id)[0]:
+                if time.monotonic() > deadline:
+                    raise TimeoutError(f"job {job_id} not done after {timeout} s")
+                time.sleep(1e-4)
         return self._keep[job_id][1]
 
     def release(self, job_id: int):

@@ -27,8 +27,10 @@ namespace {
 
 // per-instance parameters on the device
 struct InstDev {
-    int64_t off;       // first row
-    int64_t coff;      // first coordinate
+    const float* pts;  // the instance's points (dim floats per row)
+    int32_t* out;      // its labels
+    uint8_t* cout;     // its core flags (or null)
+    int64_t off;       // first row (in the concatenation of all instances)
     int32_t dim;
     float e2;
     int32_t min_pts;
@@ -47,14 +49,14 @@ __device__ __forceinline__ int find_inst(const int64_t* __restrict__ offs, int c
     return lo;
 }
 
-__device__ __forceinline__ float4 load_row(const float* __restrict__ pts, const InstDev& in, int64_t row)
+__device__ __forceinline__ float4 load_row(const InstDev& in, int64_t row)
 {
-    const float* p = pts + in.coff + (row - in.off) * in.dim;
+    const float* p = in.pts + (row - in.off) * in.dim;
     return make_float4(p[0], p[1], in.dim == 3 ? p[2] : 0.0f, 0.0f);
 }
 
 // per-instance exact bounds (order-preserving uint min/max) and a NaN/Inf flag
-__global__ void k_bbounds(const float* __restrict__ pts, const int64_t* __restrict__ offs,
+__global__ void k_bbounds(const int64_t* __restrict__ offs,
                           const InstDev* __restrict__ inst, int count, int64_t n, uint32_t* __restrict__ bounds,
                           uint32_t* __restrict__ nonfinite)
 {
@@ -68,7 +70,7 @@ __global__ void k_bbounds(const float* __restrict__ pts, const int64_t* __restri
         float4 q = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
         bool bad = false;
         if (valid) {
-            const float4 v = load_row(pts, inst[b], i);
+            const float4 v = load_row(inst[b], i);
             bad = !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z);
             p = v;
             q = v;
@@ -96,14 +98,14 @@ __global__ void k_bbounds(const float* __restrict__ pts, const int64_t* __restri
 }
 
 // key = (instance << lb) | Morton code of the point's cell in its instance's grid
-__global__ void k_bkeys(const float* __restrict__ pts, const int64_t* __restrict__ offs,
+__global__ void k_bkeys(const int64_t* __restrict__ offs,
                         const InstDev* __restrict__ inst, int count, int64_t n, int lb, uint64_t* __restrict__ keys,
                         uint32_t* __restrict__ vals)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int b = find_inst(offs, count, i);
         const InstDev in = inst[b];
-        const float4 v = load_row(pts, in, i);
+        const float4 v = load_row(in, i);
         uint32_t c[3];
         c[0] = cell_index(floorf(__fmul_rn(__fsub_rn(v.x, in.lo[0]), in.scale[0])), in.cmax[0]);
         c[1] = cell_index(floorf(__fmul_rn(__fsub_rn(v.y, in.lo[1]), in.scale[1])), in.cmax[1]);
@@ -113,13 +115,13 @@ __global__ void k_bkeys(const float* __restrict__ pts, const int64_t* __restrict
     }
 }
 
-__global__ void k_bgather(const float* __restrict__ pts, const int64_t* __restrict__ offs,
+__global__ void k_bgather(const int64_t* __restrict__ offs,
                           const InstDev* __restrict__ inst, int count, const uint32_t* __restrict__ perm, int64_t n,
                           float4* __restrict__ sp)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = perm[i];
-        sp[i] = load_row(pts, inst[find_inst(offs, count, row)], row);
+        sp[i] = load_row(inst[find_inst(offs, count, row)], row);
     }
 }
 
@@ -219,17 +221,19 @@ __global__ void k_bfinalize(int32_t* labels, const uint8_t* __restrict__ core, c
     }
 }
 
+// outputs of every instance, in its own buffers (instance-relative labels)
 __global__ void k_brelabel(const int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
-                           int64_t n, int mode, const int32_t* __restrict__ canon, int32_t* __restrict__ out,
-                           uint8_t* __restrict__ core_out)
+                           const uint64_t* __restrict__ keys, int lb, const InstDev* __restrict__ inst, int64_t n,
+                           int mode, const int32_t* __restrict__ canon)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const bool c = core[i] != 0;
         const int r = uf_root(labels, (int)i);
         const bool member = c || (mode == DBSCAN_MODE_DBSCAN && r != (int)i);
-        const uint32_t o = perm[i];
-        out[o] = member ? canon[r] : -1;
-        if (core_out) core_out[o] = c ? 1 : 0;
+        const InstDev& in = inst[keys[i] >> lb];
+        const int64_t o = (int64_t)perm[i] - in.off;
+        in.out[o] = member ? canon[r] : -1;
+        if (in.cout) in.cout[o] = c ? 1 : 0;
     }
 }
 
@@ -338,10 +342,8 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo)
 // The graph of the stages after the bounds, kept per workspace.
 struct BatchGraph {
     cudaGraphExec_t exec = nullptr;
-    // what the captured kernels were given
-    const float* points = nullptr;
-    int32_t* labels_out = nullptr;
-    uint8_t* core_out = nullptr;
+    // what the captured kernels were given (buffers of the instances are
+    // read from the device-side instance table, not captured)
     void* ws = nullptr;
     int64_t n = 0;
     int count = 0, mode = -1, algo = -1, lb = 0, key_bits = 0, max_mp = 0, block = 0;
@@ -360,13 +362,12 @@ BatchGraph* graph_of(Workspace* w)
 }
 
 // Enqueues every stage after the bounds for the given plan.
-cudaError_t enqueue_batch_stages(const BatchPlan& p, const float* points, int64_t n, int count, int mode, int algo,
-                                 int lb, int key_bits, int max_mp, int32_t* labels_out, uint8_t* core_out,
-                                 cudaStream_t s)
+cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int mode, int algo, int lb, int key_bits,
+                                 int max_mp, cudaStream_t s)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(p.ctrl + CTRL_M, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_bkeys<<<grid_n(n), 256, 0, s>>>(points, p.offs, p.inst, count, n, lb, p.keys, p.vals);
+    k_bkeys<<<grid_n(n), 256, 0, s>>>(p.offs, p.inst, count, n, lb, p.keys, p.vals);
     note_launches(1);
     SortBuffers sb;
     sb.keys_alt = p.keys_alt;
@@ -379,7 +380,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, const float* points, int64_
     if ((e = sort_pairs_u64(p.keys, p.vals, n, key_bits, sb, s, &in_alt)) != cudaSuccess) return e;
     const uint64_t* keys = in_alt ? p.keys_alt : p.keys;
     const uint32_t* perm = in_alt ? p.vals_alt : p.vals;
-    k_bgather<<<grid_n(n), 256, 0, s>>>(points, p.offs, p.inst, count, perm, n, p.sp);
+    k_bgather<<<grid_n(n), 256, 0, s>>>(p.offs, p.inst, count, perm, n, p.sp);
     note_launches(1);
     if (algo == DBSCAN_ALGO_DENSEBOX) {
         if ((e = cudaMemsetAsync(p.db.pdense, 0, (size_t)n, s)) != cudaSuccess) return e;
@@ -426,7 +427,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, const float* points, int64_
     if ((e = launch_cluster_pre(a, s)) != cudaSuccess) return e;
     if ((e = launch_cluster_main(a, s)) != cudaSuccess) return e;
     k_bfinalize<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, p.canon);
-    k_brelabel<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, n, mode, p.canon, labels_out, core_out);
+    k_brelabel<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, mode, p.canon);
     note_launches(2);
     return cudaGetLastError();
 }
@@ -434,9 +435,9 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, const float* points, int64_
 }  // namespace
 
 // Host side of dbscan_run_batch (arguments already checked).
-dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offsets, const int32_t* dims,
-                        const float* eps, const int32_t* min_pts, int32_t count, int mode, int algo,
-                        int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
+dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, const float* const* points,
+                        const int32_t* dims, const float* eps, const int32_t* min_pts, int32_t* const* labels,
+                        uint8_t* const* cores, int mode, int algo, cudaStream_t s)
 {
     const int64_t n = offsets[count];
     if (n == 0) return DBSCAN_OK;
@@ -450,20 +451,20 @@ dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offset
     std::vector<InstDev> inst((size_t)count);
     std::vector<float> e2s((size_t)count);
     std::vector<int32_t> mps((size_t)count);
-    int64_t coff = 0;
     int max_mp = 1;
     for (int b = 0; b < count; ++b) {
         InstDev& in = inst[b];
         memset(&in, 0, sizeof(in));
+        in.pts = points[b];
+        in.out = labels[b];
+        in.cout = cores ? cores[b] : nullptr;
         in.off = offsets[b];
-        in.coff = coff;
         in.dim = dims[b];
         in.e2 = eps[b] * eps[b];
         in.min_pts = min_pts[b];
         e2s[b] = in.e2;
         mps[b] = in.min_pts;
         if (in.min_pts > max_mp) max_mp = in.min_pts;
-        coff += (offsets[b + 1] - offsets[b]) * dims[b];
     }
     std::vector<uint32_t> hb(6 * (size_t)count + 1);
     for (int b = 0; b < count; ++b)
@@ -477,7 +478,7 @@ dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offset
     BTRY(cudaMemcpyAsync(p.offs, offsets, sizeof(int64_t) * ((size_t)count + 1), cudaMemcpyHostToDevice, s));
     BTRY(cudaMemcpyAsync(p.inst, inst.data(), sizeof(InstDev) * (size_t)count, cudaMemcpyHostToDevice, s));
     BTRY(cudaMemcpyAsync(p.bounds, hb.data(), sizeof(uint32_t) * hb.size(), cudaMemcpyHostToDevice, s));
-    k_bbounds<<<grid_n(n), 256, 0, s>>>(points, p.offs, p.inst, count, n, p.bounds, p.bounds + 6 * (size_t)count);
+    k_bbounds<<<grid_n(n), 256, 0, s>>>(p.offs, p.inst, count, n, p.bounds, p.bounds + 6 * (size_t)count);
     note_launches(1);
     uint32_t err = 0;
     BTRY(cudaMemcpyAsync(hb.data(), p.bounds, sizeof(uint32_t) * hb.size(), cudaMemcpyDeviceToHost, s));
@@ -552,8 +553,7 @@ dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offset
     BTRY(cudaStreamWaitEvent(gs, w->fork, 0));
     std::lock_guard<std::mutex> lk(g_graph_mu);
     BatchGraph* g = graph_of(w);
-    const bool same = g->exec && g->points == points && g->labels_out == labels_out && g->core_out == core_out &&
-                      g->ws == w->main.base && g->n == n && g->count == count && g->mode == mode && g->algo == algo &&
+    const bool same = g->exec && g->ws == w->main.base && g->n == n && g->count == count && g->mode == mode && g->algo == algo &&
                       g->lb == lb && g->key_bits == key_bits && g->max_mp == max_mp && g->block == g_tuning.block;
     if (!same) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
@@ -561,8 +561,7 @@ dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offset
         cudaGraph_t graph = nullptr;
         const int64_t before = launches_so_far();
         BTRY(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = enqueue_batch_stages(p, points, n, count, mode, algo, lb, key_bits, max_mp, labels_out,
-                                              core_out, gs);
+        cudaError_t ce = enqueue_batch_stages(p, n, count, mode, algo, lb, key_bits, max_mp, gs);
         cudaError_t ee = cudaStreamEndCapture(gs, &graph);
         if (ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -576,9 +575,6 @@ dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offset
             return cuda_error(ie, "cudaGraphInstantiate");
         }
         g->kernels = (int)(launches_so_far() - before);
-        g->points = points;
-        g->labels_out = labels_out;
-        g->core_out = core_out;
         g->ws = w->main.base;
         g->n = n;
         g->count = count;
@@ -596,6 +592,12 @@ dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offset
     BTRY(cudaStreamWaitEvent(s, w->join, 0));
 #undef BTRY
     return DBSCAN_OK;
+}
+
+size_t batch_workspace_bytes(int64_t n, int count, int algo)
+{
+    BatchPlan sizing;
+    return carve_batch(sizing, nullptr, n, count, algo);
 }
 
 void release_batch_graphs(Workspace* w)

@@ -464,6 +464,29 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
 
 using namespace gbd;
 
+namespace gbd {
+
+// the control words open every plan (single and batched), so the error word
+// sits at the same place whatever ran last
+dbscan_status workspace_status(Workspace* w, cudaStream_t s)
+{
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (!w || !w->main.base) return DBSCAN_OK;
+    uint32_t err = 0;
+    Plan p;
+    carve_plan(p, w->main.base, 0, 3, DBSCAN_ALGO_FDBSCAN);
+    TRY_CUDA(cudaMemcpyAsync(&err, p.ctrl + CTRL_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+        TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_ERR, 0, sizeof(uint32_t), s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "device error bits 0x%x", err);
+    }
+    return DBSCAN_OK;
+}
+
+}  // namespace gbd
+
 extern "C" {
 
 dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
@@ -528,25 +551,25 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
     (void)coords;
-    return run_batch(w, points, offsets, dims, eps, min_pts, count, mode, algo, labels_out, core_out, s);
+    std::vector<const float*> pp((size_t)count);
+    std::vector<int32_t*> lp((size_t)count);
+    std::vector<uint8_t*> cp((size_t)count);
+    int64_t coff = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        pp[b] = points + coff;
+        lp[b] = labels_out + offsets[b];
+        cp[b] = core_out ? core_out + offsets[b] : nullptr;
+        coff += (offsets[b + 1] - offsets[b]) * dims[b];
+    }
+    return run_batch(w, count, offsets, pp.data(), dims, eps, min_pts, lp.data(), core_out ? cp.data() : nullptr,
+                     mode, algo, s);
 }
 
 dbscan_status dbscan_stream_status(dbscan_stream stream)
 {
     t_err.clear();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    TRY_CUDA(cudaStreamSynchronize(s));
-    Workspace* w = get_workspace(s);
-    if (!w || !w->main.base) return DBSCAN_OK;
-    uint32_t err = 0;
-    Plan p;
-    carve_plan(p, w->main.base, 0, 3, DBSCAN_ALGO_FDBSCAN);
-    TRY_CUDA(cudaMemcpy(&err, p.ctrl + CTRL_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    if (err) {
-        TRY_CUDA(cudaMemset(p.ctrl + CTRL_ERR, 0, sizeof(uint32_t)));
-        return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "device error bits 0x%x", err);
-    }
-    return DBSCAN_OK;
+    return gbd::workspace_status(get_workspace(s), s);
 }
 
 dbscan_status dbscan_release_workspaces(void)

@@ -47,9 +47,16 @@ void release_stream_workspace(cudaStream_t s);
 size_t workspace_bytes(int64_t n, int dim, int algo);
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
                            int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
-dbscan_status run_batch(Workspace* w, const float* points, const int64_t* offsets, const int32_t* dims,
-                        const float* eps, const int32_t* min_pts, int32_t count, int mode, int algo,
-                        int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+// count instances: rows offsets[b]..offsets[b+1]-1 of the concatenation;
+// instance b's points, labels and core flags (cores may be null, or an entry
+// of it) are separate device buffers
+// device bytes run_batch plans for n points in count instances
+size_t batch_workspace_bytes(int64_t n, int count, int algo);
+// waits for s, then returns (and clears) the device error bits of w's arena
+dbscan_status workspace_status(Workspace* w, cudaStream_t s);
+dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, const float* const* points,
+                        const int32_t* dims, const float* eps, const int32_t* min_pts, int32_t* const* labels,
+                        uint8_t* const* cores, int mode, int algo, cudaStream_t s);
 void release_batch_graphs(Workspace* w);
 
 }  // namespace gbd

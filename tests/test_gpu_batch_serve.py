@@ -4,6 +4,7 @@ exactly, border labels within their valid sets)."""
 import numpy as np
 import pytest
 
+import oracle
 from tests.parity import assert_matches_oracle
 from workloads import batch_instances, blobs
 
@@ -11,6 +12,8 @@ torch = pytest.importorskip("torch")
 import paper_2103_05162_gb300 as gb  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+WAIT_S = 300.0  # a job still queued after this long is a failure, not a hang
 
 
 def _concat(instances):
@@ -109,3 +112,113 @@ def test_batch_rejects_nonfinite():
     with pytest.raises(gb.DbscanError) as e:
         gb.dbscan_run_batch(torch.from_numpy(flat).cuda(), offs, [3, 2], [0.05, 0.05], [3, 3])
     assert e.value.name == "NONFINITE"
+
+
+# --- serving ------------------------------------------------------------------
+
+def _serve_jobs(seed):
+    """A mix of small jobs (merged into fused batches), mid-size ones and a
+    few that run alone, in both dimensions, both algorithms and modes."""
+    rs = np.random.default_rng(seed)
+    jobs = []
+    for i in range(48):
+        d = int(rs.choice([2, 3]))
+        n = int(rs.choice([0, 1, 40, 700, 5000, 20000])) if i % 8 else int(rs.choice([300_000, 400_000]))
+        eps = float(np.float32(rs.uniform(0.01, 0.05)))
+        mp = int(rs.choice([2, 5, 10]))
+        mode = int(rs.choice([gb.MODE_DBSCAN, gb.MODE_DBSCAN_STAR]))
+        algo = int(rs.choice([gb.ALGO_FDBSCAN, gb.ALGO_DENSEBOX]))
+        pts = blobs(n, d, int(rs.integers(0, 2**31))) if n else np.zeros((0, d), np.float32)
+        jobs.append((pts, eps, mp, mode, algo))
+    return jobs
+
+
+def _serve(jobs, batching=True, slots=4, budget=8 << 30, hold=True):
+    with gb.Server(budget, max_slots=slots) as srv:
+        if not batching:
+            srv.set_batching(0, 1 << 24, 4096)
+        dev = [(torch.from_numpy(p).cuda(), torch.empty(p.shape[0], dtype=torch.uint8, device="cuda"))
+               for p, *_ in jobs]
+        torch.cuda.synchronize()
+        if hold:
+            srv.hold(True)  # queue everything first: merging is then certain
+        ids = [srv.submit(x, eps, mp, mode=mode, algo=algo, core_out=c)
+               for (x, c), (_, eps, mp, mode, algo) in zip(dev, jobs)]
+        srv.hold(False)
+        out = []
+        for jid, (_, c) in zip(ids, dev):
+            lab = srv.wait(jid, timeout=WAIT_S)
+            done, lat = srv.poll(jid)
+            assert done and lat >= 0.0
+            out.append((lab.cpu().numpy(), c.cpu().numpy()))
+            srv.release(jid)
+        stats = srv.stats()
+    return out, stats
+
+
+def test_server_jobs_match_oracle_and_batch():
+    jobs = _serve_jobs(7)
+    out, stats = _serve(jobs)
+    assert stats["done"] == sum(1 for p, *_ in jobs if p.shape[0] > 0)
+    assert stats["batches"] >= 1 and stats["batched_jobs"] >= 2, stats
+    for (pts, eps, mp, mode, algo), (lab, cor) in zip(jobs, out):
+        if 0 < pts.shape[0] <= 20000:
+            assert_matches_oracle(pts, eps, mp, mode, lab, cor)
+    # the large jobs: same as the same job run alone through dbscan_run
+    for (pts, eps, mp, mode, algo), (lab, cor) in zip(jobs, out):
+        if pts.shape[0] > 20000:
+            x = torch.from_numpy(pts).cuda()
+            c = torch.empty(pts.shape[0], dtype=torch.uint8, device="cuda")
+            alone = gb.dbscan_run(x, eps, mp, mode=mode, algo=algo, core_out=c)[0].cpu().numpy()
+            np.testing.assert_array_equal(cor, c.cpu().numpy())
+            np.testing.assert_array_equal(lab[cor.astype(bool)], alone[cor.astype(bool)])
+            np.testing.assert_array_equal(lab == -1, alone == -1)
+
+
+def test_server_result_same_alone_and_in_mix():
+    """A job's core set, core labels and noise set do not depend on which
+    jobs it was merged with, nor on whether batching is on."""
+    jobs = _serve_jobs(11)
+    mixed, st_on = _serve(jobs, batching=True, slots=3)
+    single, st_off = _serve(jobs, batching=False, slots=2)
+    assert st_on["batches"] >= 1 and st_off["batches"] == 0
+    for (pts, *_), (la, ca), (lb, cb) in zip(jobs, mixed, single):
+        np.testing.assert_array_equal(ca, cb)
+        core = ca.astype(bool)
+        np.testing.assert_array_equal(la[core], lb[core])
+        np.testing.assert_array_equal(la == -1, lb == -1)
+
+
+def test_server_budget_admission_and_rejection():
+    small = [(blobs(4000, 3, s), 0.03, 5, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX) for s in range(6)]
+    # a budget that admits about one small job at a time: jobs queue, all finish
+    out, stats = _serve(small, budget=3 << 20, slots=4, hold=False)
+    assert stats["done"] == len(small)
+    for (pts, eps, mp, mode, algo), (lab, cor) in zip(small, out):
+        assert_matches_oracle(pts, eps, mp, mode, lab, cor)
+    with gb.Server(1 << 20, max_slots=1) as srv:
+        x = torch.from_numpy(blobs(200_000, 3, 1)).cuda()
+        with pytest.raises(gb.DbscanError):
+            srv.submit(x, 0.03, 5)
+
+
+def test_server_bad_job_does_not_fail_its_batch():
+    good = [(blobs(3000, 2, s), 0.03, 5, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX) for s in range(5)]
+    bad = blobs(3000, 2, 99)
+    bad[17, 0] = np.nan
+    jobs = good[:2] + [(bad, 0.03, 5, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX)] + good[2:]
+    with gb.Server(8 << 30, max_slots=1) as srv:
+        dev = [torch.from_numpy(p).cuda() for p, *_ in jobs]
+        torch.cuda.synchronize()
+        srv.hold(True)
+        ids = [srv.submit(x, eps, mp, mode=mode, algo=algo) for x, (_, eps, mp, mode, algo) in zip(dev, jobs)]
+        srv.hold(False)
+        for k, jid in enumerate(ids):
+            if k == 2:
+                with pytest.raises(gb.DbscanError):
+                    srv.wait(jid, timeout=WAIT_S)
+            else:
+                lab = srv.wait(jid, timeout=WAIT_S).cpu().numpy()
+                p, eps, mp, mode, _ = jobs[k]
+                olab, ocore = oracle.dbscan(p, eps, mp, mode)
+                np.testing.assert_array_equal(lab[ocore], olab[ocore])
