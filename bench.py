@@ -9,6 +9,8 @@ points; the output labels stay on the device.
 
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+  python bench.py --mode batch   # one fused batch of 4096 instances vs one run each
+  python bench.py --mode serve   # Poisson-arrival serving vs sequential runs
 With N > 1 it is launched by torch.distributed.run; each rank clusters its own
 replica of the workload (replicas only: the method has no exchange step on
 one node), and the value is the points of all ranks over the slowest rank's
@@ -290,6 +292,170 @@ def run_gb300(args, rank: int, world: int) -> None:
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ batch and serve
+def run_batch_mode(args) -> None:
+    """One fused dbscan_run_batch over thousands of independent instances
+    against one dbscan_run per instance on one stream (same inputs, same
+    outputs)."""
+    import torch
+
+    import paper_2103_05162_gb300 as gb
+    from workloads import batch_instances
+
+    t0 = time.perf_counter()
+    inst = batch_instances(args.batch_count, args.seed + 1, size_scale=args.batch_scale)
+    gen_s = time.perf_counter() - t0
+    flat = np.concatenate([x.points.ravel() for x in inst]).astype(np.float32)
+    offs = np.concatenate([[0], np.cumsum([x.n for x in inst])]).astype(np.int64)
+    coffs = np.concatenate([[0], np.cumsum([x.n * x.dim for x in inst])]).astype(np.int64)
+    dims = [x.dim for x in inst]
+    eps = [x.eps for x in inst]
+    mps = [x.min_pts for x in inst]
+    pts = torch.from_numpy(flat).cuda()
+    total = int(offs[-1])
+    labels = torch.empty(total, dtype=torch.int32, device="cuda")
+    views = [pts[coffs[b]:coffs[b + 1]].view(-1, dims[b]) for b in range(len(inst))]
+    outs = [labels[offs[b]:offs[b + 1]] for b in range(len(inst))]
+    for algo_name in args.batch_algos.split(","):
+        algo = gb.ALGO_DENSEBOX if algo_name == "densebox" else gb.ALGO_FDBSCAN
+
+        def batch():
+            gb.dbscan_run_batch(pts, offs, dims, eps, mps, algo=algo, labels_out=labels)
+
+        def sequential():
+            for b in range(len(inst)):
+                if offs[b + 1] > offs[b]:
+                    gb.dbscan_run(views[b], eps[b], mps[b], algo=algo, labels_out=outs[b])
+
+        for _ in range(max(3, args.warmup)):  # direct, capture, replay
+            batch()
+        torch.cuda.synchronize()
+        launches0 = gb.kernel_launches()
+        tb = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            batch()
+            torch.cuda.synchronize()
+            tb.append(time.perf_counter() - t)
+        launches = (gb.kernel_launches() - launches0) / args.steps
+        sequential()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sequential()
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t
+        tbm = float(np.median(tb))
+        print(json.dumps({
+            "metric": "batched points clustered/sec (one fused batch vs one run per instance)",
+            "value": total / tbm, "unit": UNIT, "algo": algo_name, "instances": len(inst), "points": total,
+            "batch_ms_median": 1e3 * tbm, "batch_ms_min": 1e3 * min(tb), "sequential_ms": 1e3 * ts,
+            "sequential_points_per_s": total / ts, "speedup": ts / tbm, "gpu_launches_per_batch": launches,
+            "steps": args.steps, "timing": "wall clock around the call and a device synchronize",
+            "workload": f"batch_instances({args.batch_count}, seed={args.seed + 1}, size_scale={args.batch_scale}):"
+                        f" lognormal sizes, 2D/3D blobs, eps U[0.01,0.05], minPts U{{2,5,10}}",
+            "gen_s": round(gen_s, 1)}), flush=True)
+
+
+def _wait_until(target: float) -> float:
+    while True:
+        now = time.perf_counter()
+        if now >= target:
+            return now
+        if target - now > 2e-3:
+            time.sleep(target - now - 1e-3)
+
+
+def run_serve_mode(args) -> None:
+    """Replays Poisson arrival schedules in real time through the server
+    (continuous batching, several slots) and, on the same schedule, through
+    one dbscan_run per job in arrival order on one stream; reports latency
+    percentiles (arrival to labels complete) and throughput of both."""
+    import torch
+
+    import paper_2103_05162_gb300 as gb
+    from workloads import SERVE_POOL_N, serve_pools, serve_schedule
+
+    t0 = time.perf_counter()
+    pools = {k: torch.from_numpy(v).cuda() for k, v in serve_pools(SERVE_POOL_N, args.seed + 100).items()}
+    gen_s = time.perf_counter() - t0
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    scheds = [serve_schedule(args.serve_jobs, lam, args.seed + 1000 + i) for i, lam in enumerate(rates)]
+    cap = max(sum(j.n for j in sc) for sc in scheds)
+    arena = torch.empty(cap, dtype=torch.int32, device="cuda")
+
+    def views(sched):
+        out, o = [], 0
+        for j in sched:
+            out.append((pools[j.pool][j.offset:j.offset + j.n], arena[o:o + j.n]))
+            o += j.n
+        return out
+
+    # warm-up: every slot (and the sequential arm's stream) grows its
+    # workspace to the largest job of each family and algorithm
+    from workloads import halo_eps
+    warm = [("blobs3", 1, 0.03), ("blobs2", 1, 0.03), ("halos", 1, halo_eps(SERVE_POOL_N)),
+            ("roads", 0, float(np.float32(2e-4 * (4194304 / SERVE_POOL_N) ** 0.5)))]
+    srv = gb.Server(int(args.serve_budget_gb * (1 << 30)), max_slots=args.serve_slots)
+    srv.hold(True)
+    wids = [srv.submit(pools[p], e, 10, algo=a, labels_out=arena[:SERVE_POOL_N])
+            for _ in range(args.serve_slots) for p, a, e in warm]
+    srv.hold(False)
+    for w in wids:
+        srv.wait(w, timeout=600)
+        srv.release(w)
+    for p, a, e in warm:
+        gb.dbscan_run(pools[p], e, 10, algo=a, labels_out=arena[:SERVE_POOL_N])
+    torch.cuda.synchronize()
+
+    for lam, sched in zip(rates, scheds):
+        vs = views(sched)
+        total = sum(j.n for j in sched)
+        stats0 = srv.stats()
+        # served
+        lag, ids, sub = [], [], []
+        t0 = time.perf_counter()
+        for j, (x, lab) in zip(sched, vs):
+            target = t0 + j.arrival_s
+            now = _wait_until(target)
+            ids.append(srv.submit(x, j.eps, j.min_pts, algo=j.algo, labels_out=lab))
+            lag.append(now - target)
+            sub.append(now)
+        lat, done_at = [], []
+        for jid, lg, ts in zip(ids, lag, sub):
+            srv.wait(jid, timeout=600)
+            _, l_srv = srv.poll(jid)
+            srv.release(jid)
+            lat.append(lg + l_srv)
+            done_at.append(ts + l_srv)
+        span = max(done_at) - t0
+        st = {k: v - stats0[k] for k, v in srv.stats().items()}
+        # sequential plain runs, arrival order, one stream
+        slat, t0 = [], time.perf_counter()
+        done = t0
+        for j, (x, lab) in zip(sched, vs):
+            target = t0 + j.arrival_s
+            _wait_until(target)
+            gb.dbscan_run(x, j.eps, j.min_pts, algo=j.algo, labels_out=lab)
+            torch.cuda.synchronize()
+            done = time.perf_counter()
+            slat.append(done - target)
+        sspan = done - t0
+        lat_ms, slat_ms = 1e3 * np.asarray(lat), 1e3 * np.asarray(slat)
+        print(json.dumps({
+            "metric": "served latency, arrival to labels complete (Poisson arrivals)",
+            "rate_per_s": lam, "jobs": len(sched), "points": total, "mean_job_points": total / len(sched),
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "points_per_s": total / span, "span_s": span,
+            "sequential": {"p50_ms": float(np.percentile(slat_ms, 50)), "p99_ms": float(np.percentile(slat_ms, 99)),
+                           "points_per_s": total / sspan, "span_s": sspan},
+            "server": {"slots": args.serve_slots, "budget_gb": args.serve_budget_gb, **st},
+            "submit_lag_ms_p99": float(np.percentile(1e3 * np.asarray(lag), 99)),
+            "workload": "serve_schedule: sizes log-uniform [1e4, 8e6]; families blobs3 (DenseBox), roads "
+                        "(FDbscan), halos (DenseBox), batch instances (DenseBox); each job a window of an "
+                        f"8M-point shuffled pool; DBSCAN mode; pools generated in {gen_s:.1f} s"}), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,6 +472,16 @@ def main():
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
+                    help="step: the headline line (default); batch: fused batch vs per-instance runs; "
+                         "serve: Poisson-arrival serving vs sequential runs (1 GPU, rank 0 only)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-algos", default="densebox,fdbscan")
+    ap.add_argument("--serve-rates", default="100,300,1000,3000,5000")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -314,6 +490,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.mode != "step":
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            (run_batch_mode if args.mode == "batch" else run_serve_mode)(args)
         return
     if world > 1:
         import torch

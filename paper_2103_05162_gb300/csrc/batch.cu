@@ -340,13 +340,27 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo)
 }
 
 // The graph of the stages after the bounds, kept per workspace.
-struct BatchGraph {
-    cudaGraphExec_t exec = nullptr;
-    // what the captured kernels were given (buffers of the instances are
-    // read from the device-side instance table, not captured)
+// what a captured graph depends on (the instances' buffers are read from the
+// device-side instance table, so they are not part of it)
+struct BatchShape {
     void* ws = nullptr;
     int64_t n = 0;
     int count = 0, mode = -1, algo = -1, lb = 0, key_bits = 0, max_mp = 0, block = 0;
+    bool operator==(const BatchShape& o) const
+    {
+        return ws == o.ws && n == o.n && count == o.count && mode == o.mode && algo == o.algo && lb == o.lb &&
+               key_bits == o.key_bits && max_mp == o.max_mp && block == o.block;
+    }
+};
+
+// Per workspace: the captured graph and the shape of the previous call. A
+// shape is captured when it comes twice in a row and replayed while it
+// repeats; a shape seen once (the usual case for the server's merged jobs)
+// is launched directly, since capture and instantiation cost more than the
+// launches they save.
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    BatchShape captured, last;
     int kernels = 0;
 };
 
@@ -539,10 +553,10 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
     BTRY(cudaMemcpyAsync(p.e2s, e2s.data(), sizeof(float) * (size_t)count, cudaMemcpyHostToDevice, s));
     BTRY(cudaMemcpyAsync(p.mps, mps.data(), sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, s));
 
-    // the remaining stages run as a CUDA graph on the workspace's own stream
-    // (capture is not possible on the legacy default stream), forked from and
-    // joined back to the caller's stream; the kept graph is replayed when
-    // nothing it captured has changed
+    // the remaining stages run on the workspace's own stream (capture is not
+    // possible on the legacy default stream), forked from and joined back to
+    // the caller's stream: launched directly, or as a CUDA graph when the
+    // same shape repeats (BatchGraph)
     if (!w->gstream) {
         BTRY(cudaStreamCreateWithFlags(&w->gstream, cudaStreamNonBlocking));
         BTRY(cudaEventCreateWithFlags(&w->fork, cudaEventDisableTiming));
@@ -551,13 +565,33 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
     cudaStream_t gs = w->gstream;
     BTRY(cudaEventRecord(w->fork, s));
     BTRY(cudaStreamWaitEvent(gs, w->fork, 0));
-    std::lock_guard<std::mutex> lk(g_graph_mu);
+    std::unique_lock<std::mutex> lk(g_graph_mu);
     BatchGraph* g = graph_of(w);
-    const bool same = g->exec && g->ws == w->main.base && g->n == n && g->count == count && g->mode == mode && g->algo == algo &&
-                      g->lb == lb && g->key_bits == key_bits && g->max_mp == max_mp && g->block == g_tuning.block;
-    if (!same) {
+    BatchShape shape;
+    shape.ws = w->main.base;
+    shape.n = n;
+    shape.count = count;
+    shape.mode = mode;
+    shape.algo = algo;
+    shape.lb = lb;
+    shape.key_bits = key_bits;
+    shape.max_mp = max_mp;
+    shape.block = g_tuning.block;
+    const bool replay = g->exec && g->captured == shape;
+    const bool capture = !replay && g->last == shape;
+    g->last = shape;
+    if (!replay && !capture) {
+        lk.unlock();
+        cudaError_t ce = enqueue_batch_stages(p, n, count, mode, algo, lb, key_bits, max_mp, gs);
+        if (ce != cudaSuccess) return cuda_error(ce, "batch stages");
+        BTRY(cudaEventRecord(w->join, gs));
+        BTRY(cudaStreamWaitEvent(s, w->join, 0));
+        return DBSCAN_OK;
+    }
+    if (capture) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;
+        g->captured = BatchShape{};
         cudaGraph_t graph = nullptr;
         const int64_t before = launches_so_far();
         BTRY(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
@@ -575,15 +609,7 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
             return cuda_error(ie, "cudaGraphInstantiate");
         }
         g->kernels = (int)(launches_so_far() - before);
-        g->ws = w->main.base;
-        g->n = n;
-        g->count = count;
-        g->mode = mode;
-        g->algo = algo;
-        g->lb = lb;
-        g->key_bits = key_bits;
-        g->max_mp = max_mp;
-        g->block = g_tuning.block;
+        g->captured = shape;
     } else {
         note_launches(g->kernels);
     }

@@ -74,9 +74,10 @@ def test_batch_matches_oracle_per_instance(mode, algo):
 
 
 def test_batch_replays_with_new_contents():
-    """The second call with the same buffers and shapes replays the kept
-    graph; its per-instance parameters and points are new."""
-    for rnd in range(3):
+    """Calls with the same shapes: the first launches directly, the second
+    captures a graph, the later ones replay it -- with new points and
+    per-instance parameters each time, and new output buffers in the last."""
+    for rnd in range(4):
         rs = np.random.default_rng(100 + rnd)
         inst = [_Inst(blobs(3000, 3 if b % 2 else 2, 1000 * rnd + b), rs.uniform(0.01, 0.05),
                       int(rs.choice([2, 5, 10]))) for b in range(40)]
@@ -87,6 +88,9 @@ def test_batch_replays_with_new_contents():
             core = torch.empty(int(offs[-1]), dtype=torch.uint8, device="cuda")
         else:
             pts.copy_(torch.from_numpy(flat))
+        if rnd == 3:
+            labels = torch.full((int(offs[-1]),), -7, dtype=torch.int32, device="cuda")
+            core = torch.full((int(offs[-1]),), 9, dtype=torch.uint8, device="cuda")
         gb.dbscan_run_batch(pts, offs, [x.dim for x in inst], [x.eps for x in inst], [x.min_pts for x in inst],
                             algo=gb.ALGO_DENSEBOX, labels_out=labels, core_out=core)
         torch.cuda.synchronize()

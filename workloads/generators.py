@@ -13,7 +13,8 @@ kind of structure:
 * ``halos``     -- 3D cosmology-like particles: NFW-profile halos with a
                    power-law size distribution plus a uniform background.
 * ``batch``     -- thousands of blob instances with lognormal sizes.
-* ``serve_trace`` -- a Poisson arrival trace of jobs drawn from the above.
+* ``serve_schedule`` -- Poisson arrivals of jobs, each a window of one of
+                   the ``serve_pools`` (shuffled point sets of the above).
 
 All generators use ``numpy.random.Generator(PCG64(seed))`` and return
 C-contiguous ``float32`` arrays of shape ``(n, d)``.
@@ -26,8 +27,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "blobs", "roads", "halos", "halo_eps", "batch_instances", "serve_trace",
-    "uniform", "Instance", "Job",
+    "blobs", "roads", "halos", "halo_eps", "batch_instances", "serve_pools", "serve_schedule",
+    "uniform", "Instance", "ServeJob", "SERVE_POOL_N", "SERVE_FAMILIES",
 ]
 
 
@@ -205,47 +206,76 @@ def batch_instances(count: int, seed: int, median: float = 20000.0, sigma: float
 
 
 @dataclass
-class Job:
-    """One request of a serving trace."""
+class ServeJob:
+    """One request of a serving schedule: ``n`` rows of pool ``pool`` starting
+    at row ``offset``, clustered with ``eps``, ``min_pts`` and ``algo``."""
     arrival_s: float
     family: str
-    points: np.ndarray = field(repr=False)
+    pool: str
+    offset: int
+    n: int
     eps: float
     min_pts: int
     algo: int
 
 
-def serve_trace(n_jobs: int, rate_per_s: float, seed: int, size_range: tuple[int, int] = (10_000, 8_000_000),
-                families: tuple[str, ...] = ("blobs3", "roads", "halos", "batch")) -> list[Job]:
+SERVE_POOL_N = 8_000_000
+SERVE_FAMILIES = ("blobs3", "roads", "halos", "batch")
+
+
+def serve_pools(n: int, seed: int) -> dict[str, np.ndarray]:
+    """The shuffled point pools the jobs of a serving schedule read from:
+    3D and 2D blobs, roads and halos, ``n`` points each (the halo count
+    scaled from 50,000 halos per 2^24 points). As every pool is shuffled, a
+    window of ``k`` consecutive rows is a uniform random subsample."""
+    r = _rng(seed)
+    s = r.integers(0, 2**62, size=4)
+    return {
+        "blobs3": blobs(n, 3, int(s[0])),
+        "blobs2": blobs(n, 2, int(s[1])),
+        "roads": roads(n, int(s[2])),
+        "halos": halos(n, int(s[3]), n_halos=max(10, int(round(50000 * n / 2**24)))),
+    }
+
+
+def serve_schedule(n_jobs: int, rate_per_s: float, seed: int, pool_n: int = SERVE_POOL_N,
+                   size_range: tuple[int, int] = (10_000, 8_000_000),
+                   families: tuple[str, ...] = SERVE_FAMILIES) -> list[ServeJob]:
     """Poisson arrivals of jobs drawn from the workload families.
 
     Inter-arrival times are exponential with mean ``1/rate_per_s``; sizes
-    are log-uniform on ``size_range``; the family is uniform over
-    ``families``. For ``roads`` and ``halos`` the linking length is rescaled
-    with the size so the point density per neighbourhood is kept
-    (``eps * (n_ref / n)^(1/d)``).
+    are log-uniform on ``size_range`` (capped at ``pool_n``); the family is
+    uniform over ``families``; each job reads a random window of its pool.
+
+    * ``blobs3``: 3D blobs, eps 0.03, minPts 5, DenseBox.
+    * ``roads``: eps rescaled with the size so that the point density per
+      neighbourhood is kept (``2e-4 * (4194304 / n)^(1/2)``), minPts 10,
+      FDbscan.
+    * ``halos``: eps ``halo_eps(n)``, minPts 10, DenseBox.
+    * ``batch``: one instance of a batch -- blobs in 2D or 3D (uniform), eps
+      uniform in [0.01, 0.05], minPts uniform in {2, 5, 10}, DenseBox.
     """
     r = _rng(seed)
     t = np.cumsum(r.exponential(1.0 / rate_per_s, size=n_jobs))
     sizes = np.exp(r.uniform(math.log(size_range[0]), math.log(size_range[1]), size=n_jobs)).astype(np.int64)
+    sizes = np.minimum(sizes, pool_n)
     fam = r.choice(len(families), size=n_jobs)
-    seeds = r.integers(0, 2**62, size=n_jobs)
+    u = r.uniform(0.0, 1.0, size=(n_jobs, 4))
     jobs = []
     for i in range(n_jobs):
         f = families[int(fam[i])]
         n = int(sizes[i])
-        s = int(seeds[i])
+        off = int(u[i, 0] * (pool_n - n + 1))
         if f == "blobs3":
-            jobs.append(Job(float(t[i]), f, blobs(n, 3, s), 0.03, 5, 1))
+            jobs.append(ServeJob(float(t[i]), f, "blobs3", off, n, float(np.float32(0.03)), 5, 1))
         elif f == "roads":
             eps = float(np.float32(2e-4 * (4194304 / n) ** 0.5))
-            jobs.append(Job(float(t[i]), f, roads(n, s), eps, 10, 0))
+            jobs.append(ServeJob(float(t[i]), f, "roads", off, n, eps, 10, 0))
         elif f == "halos":
-            jobs.append(Job(float(t[i]), f, halos(n, s, n_halos=max(10, n // 335)), halo_eps(n), 10, 1))
+            jobs.append(ServeJob(float(t[i]), f, "halos", off, n, halo_eps(n), 10, 1))
         else:
-            rr = _rng(s)
-            d = int(rr.choice([2, 3]))
-            eps = float(np.float32(rr.uniform(0.01, 0.05)))
-            mp = int(rr.choice([2, 5, 10]))
-            jobs.append(Job(float(t[i]), f, blobs(n, d, s), eps, mp, 1))
+            pool = "blobs2" if u[i, 1] < 0.5 else "blobs3"
+            eps = float(np.float32(0.01 + 0.04 * u[i, 2]))
+            mp = (2, 5, 10)[min(2, int(u[i, 3] * 3))]
+            jobs.append(ServeJob(float(t[i]), f, pool, off, n, eps, mp, 1))
     return jobs
