@@ -282,6 +282,7 @@ struct BatchPlan {
     int2* range;
     uint8_t* lsolid;
     int32_t* klist;
+    int32_t* tstart;
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
@@ -326,6 +327,7 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo)
     p.range = c.take<int2>(n);
     p.lsolid = c.take<uint8_t>(n);
     p.klist = c.take<int32_t>(n);
+    p.tstart = c.take<int32_t>(n);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
@@ -419,6 +421,9 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     a.leafr = p.leafr;
     a.lsolid = p.lsolid;
     a.klist = p.klist;
+    a.tstart = p.tstart;
+    a.parent = p.parent;
+    a.nmeta = p.nmeta;
     a.pdense = p.db.pdense;
     a.dstart = p.db.dstart;
     a.perm = perm;
@@ -438,6 +443,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     a.e2s = p.e2s;
     a.mps = p.mps;
     a.iroot = p.iroot;
+    if ((e = launch_cluster_starts(a, s)) != cudaSuccess) return e;
     if ((e = launch_cluster_pre(a, s)) != cudaSuccess) return e;
     if ((e = launch_cluster_main(a, s)) != cudaSuccess) return e;
     k_bfinalize<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, p.canon);

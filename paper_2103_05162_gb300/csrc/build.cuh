@@ -132,8 +132,16 @@ struct ClusterArgs {
     const float* e2s = nullptr;
     const int32_t* mps = nullptr;
     const int32_t* iroot = nullptr;
+    // tree links (parent of every node, children of internal nodes) and the
+    // per-leaf traversal start written by launch_cluster_pre
+    const int32_t* parent = nullptr;
+    const int4* nmeta = nullptr;
+    int32_t* tstart = nullptr;
 };
 cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s);
+// per-leaf traversal starts (needed by both traversal phases)
+cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s);
+// preprocessing (minPts > 2; nothing otherwise)
 cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);

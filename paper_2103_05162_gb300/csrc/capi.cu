@@ -137,6 +137,7 @@ struct Plan {
     int32_t* visit;
     uint8_t* lsolid;
     int32_t* klist;
+    int32_t* tstart;
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
@@ -184,6 +185,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
     p.visit = c.take<int32_t>(mc);
     p.lsolid = c.take<uint8_t>(mc);
     p.klist = c.take<int32_t>(mc);
+    p.tstart = c.take<int32_t>(mc);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
@@ -428,6 +430,9 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     a.leafr = p.leafr;
     a.lsolid = p.lsolid;
     a.klist = p.klist;
+    a.tstart = p.tstart;
+    a.parent = p.parent;
+    a.nmeta = p.nmeta;
     a.pdense = algo == DBSCAN_ALGO_DENSEBOX ? p.db.pdense : nullptr;
     a.dstart = algo == DBSCAN_ALGO_DENSEBOX ? p.db.dstart : nullptr;
     a.perm = perm;
@@ -445,6 +450,7 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     a.block = g_tuning.block;
     T.begin(ST_INIT);
     TRY_CUDA(launch_cluster_init(a, s));
+    TRY_CUDA(launch_cluster_starts(a, s));
     T.end();
     if (min_pts > 2) {
         T.begin(ST_PRE);

@@ -565,7 +565,22 @@ struct DevArgs {
     const float* e2s;
     const int32_t* mps;
     const int32_t* iroot;
+    // per leaf: the node its traversals start at (k_tile_start)
+    int32_t* tstart;
 };
+
+template <int D>
+__device__ __forceinline__ float box_box(const typename Traits<D>::Box& a, const typename Traits<D>::Box& b);
+template <>
+__device__ __forceinline__ float box_box<3>(const Traits<3>::Box& a, const Traits<3>::Box& b)
+{
+    return Traits<3>::box_box_dist2(a, b.lo.x, b.lo.y, b.lo.z, b.hi.x, b.hi.y, b.hi.z);
+}
+template <>
+__device__ __forceinline__ float box_box<2>(const Traits<2>::Box& a, const Traits<2>::Box& b)
+{
+    return Traits<2>::box_box_dist2(a, b.lo.x, b.lo.y, b.hi.x, b.hi.y);
+}
 
 // eps^2, minPts and the traversal start of the tile's instance
 struct TileParams {
@@ -579,6 +594,43 @@ __device__ __forceinline__ TileParams tile_params(const DevArgs<D>& a, int L)
     if (!a.linst) return TileParams{a.e2, a.min_pts, 0};
     const int b = a.linst[L];
     return TileParams{a.e2s[b], a.mps[b], a.iroot[b]};
+}
+
+// The lowest ancestor A of each leaf such that no point outside A's subtree
+// is within eps of the leaf's box: walking up from the leaf, every sibling
+// subtree whose box is within eps of the leaf box (box-to-box distance, the
+// same exact pruning test as the traversal) moves the start up to the
+// sibling's parent. Traversals for the leaf's points (each within the leaf
+// box) then start at A instead of the root and skip the levels above it,
+// where only one path could lead to a neighbour.
+template <int D>
+__global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, const int4* __restrict__ nmeta)
+{
+    using T = Traits<D>;
+    const int64_t m = a.ctrl[CTRL_M];
+    const int leaf0 = (int)(m - 1);
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < m; L += (int64_t)gridDim.x * blockDim.x) {
+        const TileParams tp = tile_params(a, (int)L);
+        int cur = leaf0 + (int)L;
+        int start = cur;
+        const typename T::Box tb = a.nodebox[cur];
+        // the depth of a tree over 64-bit keys with index tie-breaks is
+        // below STACK; a longer walk means a corrupt tree: start at the root
+        int steps = 0;
+        while (cur != tp.start) {
+            const int p = parent[cur];
+            if (p < 0 || ++steps > STACK) {
+                start = tp.start;
+                break;
+            }
+            const int4 nm = nmeta[p];
+            const int sib = nm.x == cur ? nm.y : nm.x;
+            const typename T::Box sb = a.nodebox[sib];
+            if (box_box<D>(tb, sb) <= tp.e2) start = p;
+            cur = p;
+        }
+        a.tstart[L] = start;
+    }
 }
 
 __device__ __forceinline__ int next_leaf(uint32_t* ctr)
@@ -623,7 +675,7 @@ __global__ void k_pre(DevArgs<D> a)
         v.act = counts && cnt < tp.min_pts;
         v.p = p;
         v.cnt = cnt;
-        if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
+        if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         if (counts) {
             a.core[q] = v.cnt >= tp.min_pts ? 1 : 0;
             a.nbr[q] = v.cnt >= 2 ? 1 : 0;  // another point within eps (the count includes q)
@@ -775,7 +827,7 @@ __global__ void k_main(DevArgs<D> a)
             // eps takes part in no pair, and in DBSCAN* no non-core point does
             v.valid = in && (tp.min_pts <= 2 || v.qcore || (a.mode == DBSCAN_MODE_DBSCAN && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
-            if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
+            if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         } else if (KIND == 1) {
             MainSolidV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
@@ -784,14 +836,14 @@ __global__ void k_main(DevArgs<D> a)
             v.p = a.sp[v.valid ? s + lane : s];
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         } else {
             MainBoxV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
             v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, tp.start);
+            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         }
     }
 }
@@ -868,6 +920,7 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.e2s = a.e2s;
     d.mps = a.mps;
     d.iroot = a.iroot;
+    d.tstart = a.tstart;
     return d;
 }
 
@@ -919,6 +972,16 @@ cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
     k_init<<<(unsigned)gn, 256, 0, s>>>(a.pdense, a.dstart, a.n, a.min_pts, a.labels, a.core);
     note_launches(1);
     if ((e = cudaMemsetAsync(a.canon, 0x7f, sizeof(int32_t) * (size_t)a.n, s)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
+{
+    int64_t gm = (a.m_cap + 255) / 256;
+    if (gm > 152 * 8) gm = 152 * 8;
+    if (a.dim == 3) k_tile_start<3><<<(unsigned)gm, 256, 0, s>>>(dev_args<3>(a), a.parent, a.nmeta);
+    else k_tile_start<2><<<(unsigned)gm, 256, 0, s>>>(dev_args<2>(a), a.parent, a.nmeta);
+    note_launches(1);
     return cudaGetLastError();
 }
 
