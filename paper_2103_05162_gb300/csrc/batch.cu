@@ -293,9 +293,10 @@ struct BatchPlan {
     float* e2s;         // count
     int32_t* mps;       // count
     int32_t* iroot;     // count
+    int32_t* nlist;     // n * lcap
 };
 
-size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo)
+size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo, int lcap)
 {
     BCarver c(base);
     p.ctrl = c.take<uint32_t>(CTRL_WORDS);
@@ -338,6 +339,7 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo)
     p.e2s = c.take<float>((size_t)count);
     p.mps = c.take<int32_t>((size_t)count);
     p.iroot = c.take<int32_t>((size_t)count);
+    p.nlist = c.take<int32_t>(n * lcap);
     return c.off + 256;
 }
 
@@ -430,6 +432,8 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     a.labels = p.labels;
     a.core = p.core;
     a.nbr = p.nbr;
+    a.nlist = p.nlist;
+    a.lcap = list_cap(max_mp, mode);
     a.canon = p.canon;
     a.ctrl = p.ctrl;
     a.n = n;
@@ -461,17 +465,21 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
 {
     const int64_t n = offsets[count];
     if (n == 0) return DBSCAN_OK;
+    int max_mp = 1;
+    for (int b = 0; b < count; ++b)
+        if (min_pts[b] > max_mp) max_mp = min_pts[b];
+    // one list capacity for the batch (instances with minPts <= 2 keep none)
+    const int lcap = list_cap(max_mp, mode);
     BatchPlan sizing;
-    cudaError_t e = ensure_arena(w->main, carve_batch(sizing, nullptr, n, count, algo), s);
+    cudaError_t e = ensure_arena(w->main, carve_batch(sizing, nullptr, n, count, algo, lcap), s);
     if (e != cudaSuccess) return cuda_error(e, "batch workspace");
     BatchPlan p;
-    carve_batch(p, w->main.base, n, count, algo);
+    carve_batch(p, w->main.base, n, count, algo, lcap);
 
     // per-instance static parameters, then the bounds
     std::vector<InstDev> inst((size_t)count);
     std::vector<float> e2s((size_t)count);
     std::vector<int32_t> mps((size_t)count);
-    int max_mp = 1;
     for (int b = 0; b < count; ++b) {
         InstDev& in = inst[b];
         memset(&in, 0, sizeof(in));
@@ -484,7 +492,6 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
         in.min_pts = min_pts[b];
         e2s[b] = in.e2;
         mps[b] = in.min_pts;
-        if (in.min_pts > max_mp) max_mp = in.min_pts;
     }
     std::vector<uint32_t> hb(6 * (size_t)count + 1);
     for (int b = 0; b < count; ++b)
@@ -626,10 +633,10 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
     return DBSCAN_OK;
 }
 
-size_t batch_workspace_bytes(int64_t n, int count, int algo)
+size_t batch_workspace_bytes(int64_t n, int count, int algo, int lcap)
 {
     BatchPlan sizing;
-    return carve_batch(sizing, nullptr, n, count, algo);
+    return carve_batch(sizing, nullptr, n, count, algo, lcap);
 }
 
 void release_batch_graphs(Workspace* w)

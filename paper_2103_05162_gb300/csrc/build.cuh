@@ -115,7 +115,10 @@ struct ClusterArgs {
     const uint32_t* perm;  // sorted position -> input index
     int32_t* labels;       // n (union-find parents, sorted index space)
     uint8_t* core;         // n (sorted order)
-    uint8_t* nbr;          // n: 1 if another point is within eps (set by preprocessing)
+    uint8_t* nbr;          // n: preprocessing's out-of-tile neighbour count of non-core points (lists on),
+                           //    else 1 if another point is within eps
+    int32_t* nlist = nullptr;  // n * lcap: out-of-tile neighbours found by preprocessing
+    int lcap = 0;              // list entries per point (0: no lists)
     int32_t* canon;        // n (smallest input index per root)
     uint32_t* ctrl;
     int64_t n;

@@ -142,6 +142,7 @@ struct Plan {
     uint8_t* core;
     uint8_t* nbr;
     int32_t* canon;
+    int32_t* nlist;  // n * lcap neighbour indices (preprocessing lists)
 };
 
 int64_t leaf_cap(int64_t n, int algo)
@@ -150,7 +151,7 @@ int64_t leaf_cap(int64_t n, int algo)
     return n;  // tiles hold 1..TILE points, dense cells any number
 }
 
-size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
+size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap)
 {
     Carver c(base);
     const int64_t mc = leaf_cap(n, algo);
@@ -190,13 +191,14 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo)
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
     p.canon = c.take<int32_t>(n);
+    p.nlist = c.take<int32_t>(n * lcap);
     return c.off + 256;
 }
 
-size_t workspace_bytes(int64_t n, int dim, int algo)
+size_t workspace_bytes(int64_t n, int dim, int algo, int min_pts, int mode)
 {
     Plan p;
-    return carve_plan(p, nullptr, n, dim, algo);
+    return carve_plan(p, nullptr, n, dim, algo, list_cap(min_pts, mode));
 }
 
 // ---------------------------------------------------------------------------
@@ -341,9 +343,10 @@ enum Stage { ST_BOUNDS, ST_KEYS, ST_SORT, ST_GATHER, ST_LEAVES, ST_LBVH, ST_INIT
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
                            int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
 {
-    TRY_CUDA(ensure_arena(w->main, workspace_bytes(n, dim, algo), s));
+    const int lcap = list_cap(min_pts, mode);
+    TRY_CUDA(ensure_arena(w->main, workspace_bytes(n, dim, algo, min_pts, mode), s));
     Plan p;
-    carve_plan(p, w->main.base, n, dim, algo);
+    carve_plan(p, w->main.base, n, dim, algo, lcap);
 
     StageTimer T(w, s);
     // K1 bounds, then one host wait for them
@@ -439,6 +442,8 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     a.labels = p.labels;
     a.core = p.core;
     a.nbr = p.nbr;
+    a.nlist = p.nlist;
+    a.lcap = lcap;
     a.canon = p.canon;
     a.ctrl = p.ctrl;
     a.n = n;
@@ -480,7 +485,7 @@ dbscan_status workspace_status(Workspace* w, cudaStream_t s)
     if (!w || !w->main.base) return DBSCAN_OK;
     uint32_t err = 0;
     Plan p;
-    carve_plan(p, w->main.base, 0, 3, DBSCAN_ALGO_FDBSCAN);
+    carve_plan(p, w->main.base, 0, 3, DBSCAN_ALGO_FDBSCAN, 0);
     TRY_CUDA(cudaMemcpyAsync(&err, p.ctrl + CTRL_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     TRY_CUDA(cudaStreamSynchronize(s));
     if (err) {

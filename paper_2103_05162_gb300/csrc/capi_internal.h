@@ -44,14 +44,22 @@ Workspace* get_workspace(cudaStream_t s);
 cudaError_t ensure_arena(Arena& a, size_t bytes, cudaStream_t s);
 void free_workspace(Workspace* w);
 void release_stream_workspace(cudaStream_t s);
-size_t workspace_bytes(int64_t n, int dim, int algo);
+// Neighbour lists of preprocessing (DBSCAN mode, 3 <= minPts <= 32): every
+// point keeps up to minPts - 1 of its neighbours outside its own tile, which
+// is all of them when it ends non-core; 0 means no lists.
+constexpr int LIST_MAX_MINPTS = 32;
+inline int list_cap(int min_pts, int mode)
+{
+    return (mode == DBSCAN_MODE_DBSCAN && min_pts > 2 && min_pts <= LIST_MAX_MINPTS) ? min_pts - 1 : 0;
+}
+size_t workspace_bytes(int64_t n, int dim, int algo, int min_pts, int mode);
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
                            int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
 // count instances: rows offsets[b]..offsets[b+1]-1 of the concatenation;
 // instance b's points, labels and core flags (cores may be null, or an entry
 // of it) are separate device buffers
 // device bytes run_batch plans for n points in count instances
-size_t batch_workspace_bytes(int64_t n, int count, int algo);
+size_t batch_workspace_bytes(int64_t n, int count, int algo, int lcap);
 // waits for s, then returns (and clears) the device error bits of w's arena
 dbscan_status workspace_status(Workspace* w, cudaStream_t s);
 dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, const float* const* points,

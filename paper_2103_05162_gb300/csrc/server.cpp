@@ -74,7 +74,8 @@ struct dbscan_server {
     size_t pick_locked(std::vector<Job*>& group)
     {
         return pick_group(queue, group, used, budget, lim, [&](int64_t pts, int count) {
-            return batch_workspace_bytes(pts, count, group[0]->algo);
+            // list capacity of the largest minPts a batch can have
+            return batch_workspace_bytes(pts, count, group[0]->algo, LIST_MAX_MINPTS - 1);
         });
     }
 
@@ -230,7 +231,7 @@ dbscan_status dbscan_server_submit(dbscan_server* srv, const float* points, int6
     if (!srv || !job_id_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null server or job id pointer");
     dbscan_status st = check_run_args(points, n, dim, eps, min_pts, mode, algo, labels_out);
     if (st != DBSCAN_OK) return st;
-    const size_t bytes = n > 0 ? workspace_bytes(n, dim, algo) : 0;
+    const size_t bytes = n > 0 ? workspace_bytes(n, dim, algo, min_pts, mode) : 0;
     if (bytes > srv->budget)
         return set_error(DBSCAN_ERR_INVALID_ARG, "job needs %zu bytes of device memory, above the budget of %zu",
                          bytes, srv->budget);

@@ -199,6 +199,19 @@ struct PreV {
     P p;
     bool act;
     int cnt;
+    // neighbour lists (null: none): lane l's query (point qs + l) records
+    // its out-of-tile neighbours while its count is below minPts, so a query
+    // that ends non-core has all of them (nl <= minPts - 1 = lcap)
+    int32_t* nlist;
+    int lcap;
+    int qs;
+    int nl;
+
+    __device__ __forceinline__ void note(int idx)
+    {
+        if (nl < lcap) nlist[(int64_t)(qs + lane) * lcap + nl] = idx;
+        ++nl;
+    }
 
     __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return act && NB<D>::pl(n, p) <= e2; }
     __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return act && NB<D>::pr(n, p) <= e2; }
@@ -215,6 +228,8 @@ struct PreV {
         if (cont) {
             cnt += e - s;
             if (cnt >= min_pts) act = false;
+            else if (nlist)
+                for (int u = s; u < e; ++u) note(u);
         }
         mask &= ~__ballot_sync(FULL, cont);
         for (int c = s; c < e && mask; c += 32) {
@@ -229,8 +244,14 @@ struct PreV {
                     mm &= mm - 1;
                     const P pq = NB<D>::shfl(p, q);
                     const unsigned h = __ballot_sync(FULL, in && dist2(pq, rp) <= e2);
+                    if (nlist) {
+                        // each hit leaf point writes itself into q's list
+                        const int at = __shfl_sync(FULL, nl, q) + __popc(h & ((1u << lane) - 1u));
+                        if (((h >> lane) & 1u) && at < lcap) nlist[(int64_t)(qs + q) * lcap + at] = c + lane;
+                    }
                     if (lane == q) {
                         cnt += __popc(h);
+                        nl += __popc(h);
                         if (cnt >= min_pts) act = false;
                     }
                 }
@@ -240,9 +261,12 @@ struct PreV {
                 __syncwarp();
                 if ((mask >> lane) & 1u) {
                     for (int u = 0; u < k; ++u) {
-                        if (dist2(p, buf[u]) <= e2 && ++cnt >= min_pts) {
-                            act = false;
-                            break;
+                        if (dist2(p, buf[u]) <= e2) {
+                            if (nlist) note(c + u);
+                            if (++cnt >= min_pts) {
+                                act = false;
+                                break;
+                            }
                         }
                     }
                 }
@@ -261,7 +285,9 @@ struct Rule {
     int* labels;
     uint8_t* core;
     int min_pts;
-    int mode;
+    // core-to-non-core claims: DBSCAN mode, and no preprocessing lists (with
+    // lists every border point has already claimed a core neighbour)
+    bool claims;
 
     __device__ __forceinline__ void unite(int a, int b) const
     {
@@ -280,7 +306,7 @@ struct Rule {
             if (lb == last) return;
             unite(a, b);
             last = lb;
-        } else if (mode == DBSCAN_MODE_DBSCAN) {
+        } else if (claims) {
             if (acore) uf_claim(labels, b, a);
             else if (bcore) uf_claim(labels, a, b);
         }
@@ -290,7 +316,7 @@ struct Rule {
     __device__ __forceinline__ bool need_solid(int x, bool xcore, int s) const
     {
         if (min_pts <= 2 || xcore) return uf_find(labels, x) != uf_find(labels, s);
-        return mode == DBSCAN_MODE_DBSCAN && __ldcg(labels + x) == x;
+        return claims && __ldcg(labels + x) == x;
     }
     __device__ __forceinline__ void join_solid(int x, bool xcore, int s) const
     {
@@ -555,6 +581,8 @@ struct DevArgs {
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
+    int32_t* nlist;
+    int lcap;
     uint32_t* ctrl;
     float e2;
     int min_pts;
@@ -675,10 +703,39 @@ __global__ void k_pre(DevArgs<D> a)
         v.act = counts && cnt < tp.min_pts;
         v.p = p;
         v.cnt = cnt;
+        v.nlist = a.lcap > 0 ? a.nlist : nullptr;
+        v.lcap = a.lcap;
+        v.qs = s;
+        v.nl = 0;
         if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         if (counts) {
-            a.core[q] = v.cnt >= tp.min_pts ? 1 : 0;
-            a.nbr[q] = v.cnt >= 2 ? 1 : 0;  // another point within eps (the count includes q)
+            const bool c = v.cnt >= tp.min_pts;
+            a.core[q] = c ? 1 : 0;
+            // lists: how many out-of-tile neighbours the list of a non-core
+            // point holds; else whether another point is within eps (the
+            // count includes q)
+            a.nbr[q] = a.lcap > 0 ? (c ? 0 : (uint8_t)v.nl) : (v.cnt >= 2 ? 1 : 0);
+        }
+    }
+}
+
+// Border claims from preprocessing's lists (DBSCAN mode): a non-core point
+// holds all its neighbours outside its tile; it joins the cluster of the
+// first core one (Algorithm 3's claim of a border point, Sec. 3.2, made here
+// from the border's side). Neighbours inside the tile are k_intra's.
+__global__ void k_list_claims(const int32_t* __restrict__ nlist, int lcap, const uint8_t* __restrict__ nbr,
+                              const uint8_t* __restrict__ core, int32_t* labels, int64_t n)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        if (core[q]) continue;
+        const int k = nbr[q];
+        const int32_t* row = nlist + q * lcap;
+        for (int j = 0; j < k; ++j) {
+            const int y = row[j];
+            if (core[y]) {
+                uf_claim(labels, (int)q, y);
+                break;
+            }
         }
     }
 }
@@ -798,8 +855,10 @@ __global__ void k_kinds_write(const int2* __restrict__ leafr, const uint8_t* __r
 
 // The main phase for the leaves of one kind (KIND 0: MainPtV, 1: MainSolidV,
 // 2: MainBoxV), taken from the kind's list through a work counter.
+// (56 registers: nine 128-thread blocks per SM; measured faster than the
+// unconstrained 60-64 on the 16M halo workload)
 template <int D, int KIND>
-__global__ void k_main(DevArgs<D> a)
+__global__ void __maxnreg__(56) k_main(DevArgs<D> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
@@ -813,7 +872,8 @@ __global__ void k_main(DevArgs<D> a)
         if (idx >= cnt) break;
         const int L = a.klist[off + idx];
         const TileParams tp = tile_params(a, L);
-        const Rule rule{a.labels, a.core, tp.min_pts, a.mode};
+        const bool listed = a.lcap > 0 && tp.min_pts > 2;
+        const Rule rule{a.labels, a.core, tp.min_pts, a.mode == DBSCAN_MODE_DBSCAN && !listed};
         const int2 r = a.leafr[L];
         const int s = r.x, e = r.y & 0x7fffffff;
         if (KIND == 0) {
@@ -825,7 +885,9 @@ __global__ void k_main(DevArgs<D> a)
             v.qcore = in && a.core[v.q];
             // after preprocessing a non-core point with no other point within
             // eps takes part in no pair, and in DBSCAN* no non-core point does
-            v.valid = in && (tp.min_pts <= 2 || v.qcore || (a.mode == DBSCAN_MODE_DBSCAN && a.nbr[v.q]));
+            // (with lists, non-core points took their pairs with core points
+            // from their lists and need no traversal)
+            v.valid = in && (tp.min_pts <= 2 || v.qcore || (rule.claims && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
             if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         } else if (KIND == 1) {
@@ -910,6 +972,8 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.lsolid = a.lsolid;
     d.klist = a.klist;
     d.nbr = a.nbr;
+    d.nlist = a.nlist;
+    d.lcap = a.lcap;
     d.labels = a.labels;
     d.core = a.core;
     d.ctrl = a.ctrl;
@@ -988,8 +1052,17 @@ cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
 cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
 {
     if (a.min_pts <= 2) return cudaSuccess;  // Algorithm 3: no preprocessing for minPts <= 2
+    cudaError_t e;
+    // points that keep no list (instances of a batch with minPts <= 2) read 0
+    if (a.lcap > 0 && (e = cudaMemsetAsync(a.nbr, 0, (size_t)a.n, s)) != cudaSuccess) return e;
     if (a.dim == 3) run_pre<3>(a, s); else run_pre<2>(a, s);
     note_launches(1);
+    if (a.lcap > 0) {
+        int64_t gn = (a.n + 255) / 256;
+        if (gn > 152 * 16) gn = 152 * 16;
+        k_list_claims<<<(unsigned)gn, 256, 0, s>>>(a.nlist, a.lcap, a.nbr, a.core, a.labels, a.n);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 
