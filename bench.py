@@ -56,6 +56,31 @@ def bytes_model(n: int, d: int, m: int, key_bytes: int) -> dict:
     }
 
 
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_pre_k_main_densebox_halos8m.md")
+TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2103_05162_gb300", "csrc", f)
+                   for f in ("traverse.cu", "internal.cuh", "build.cuh")]
+
+
+def measured_traffic(n: int) -> float | None:
+    """DRAM bytes (read + write) of one k_pre launch on n points of the halo
+    workload (DenseBox, minPts 10), from the committed ncu summary, scaled by
+    the points; None if the summary is missing or the traversal sources have
+    changed since it was taken."""
+    import hashlib
+    import re
+    try:
+        text = open(TRAFFIC_SUMMARY).read()
+        per_point = float(re.search(r"^traffic_bytes_per_point:\s*([0-9.]+)", text, re.M).group(1))
+        want = re.search(r"^sources_sha256:\s*([0-9a-f]{64})", text, re.M).group(1)
+        h = hashlib.sha256()
+        for f in TRAFFIC_SOURCES:
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+        return per_point * n if h.hexdigest() == want else None
+    except Exception:
+        return None
+
+
 def measured_peak_hbm() -> tuple[float, str]:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -141,6 +166,19 @@ def time_oracle(W: np.ndarray, eps: float, min_pts: int) -> float:
     return time.perf_counter() - t
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x of all ranks (the slowest rank's time); x itself on one
+    rank. device: where the reduction tensor lives (cuda for NCCL, cpu for
+    gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # -------------------------------------------------------------------- main arms
 def run_reference(args, rank: int) -> None:
     """The oracle (plain single-threaded C) on the host cores, on a bounded
@@ -220,11 +258,7 @@ def run_gb300(args, rank: int, world: int) -> None:
     clocks = sampler.stop()
     prof = gb.profile_collect(stream)
     gb.profile_enable(False)
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     value = n * world * args.steps / (ms / 1e3)
 
     # end to end through the host-buffer entry point: H2D of the points, the
@@ -241,11 +275,7 @@ def run_gb300(args, rank: int, world: int) -> None:
         e2e_steps = max(3, args.steps // 2)
         for _ in range(e2e_steps):
             gb.dbscan_run_host(hp, eps, args.min_pts, algo=algo, labels_out=hl, stream=stream)
-        e2e_s = time.perf_counter() - te
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - te, world, dev)
         e2e = {"value": n * world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
                "d2h_bytes_per_step": int(4 * n)}
 
@@ -258,9 +288,14 @@ def run_gb300(args, rank: int, world: int) -> None:
     peak, peak_kind = measured_peak_hbm()
     achieved = model[top] / (stage_ms[top] / 1e3) / 1e9
     path_bytes = sum(model[k] for k in stage_ms)
+    traffic = None
+    if top == "preprocess" and algo == gb.ALGO_DENSEBOX and args.min_pts == 10:
+        traffic = measured_traffic(n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": top, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": model[top], "launch_ms": stage_ms[top]}
+                "traffic": traffic, "kernel": "k_pre" if top == "preprocess" else top, "stage": top,
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": model[top], "launch_ms": stage_ms[top],
+                "traffic_source": "profiles/k_pre_k_main_densebox_halos8m.md (8M capture scaled by points)"
+                if traffic is not None else None}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
