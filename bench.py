@@ -11,6 +11,7 @@ Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
   python bench.py --mode batch   # one fused batch of 4096 instances vs one run each
   python bench.py --mode serve   # Poisson-arrival serving vs sequential runs
+  python bench.py --mode sweep   # several minPts over one index vs one run each
 With N > 1 it is launched by torch.distributed.run; each rank clusters its own
 replica of the workload (replicas only: the method has no exchange step on
 one node), and the value is the points of all ranks over the slowest rank's
@@ -391,6 +392,48 @@ def run_batch_mode(args) -> None:
             "gen_s": round(gen_s, 1)}), flush=True)
 
 
+def run_sweep_mode(args) -> None:
+    """One dbscan_run_multi over several minPts against one dbscan_run per
+    minPts, on the benchmark workload (CUDA events, inputs resident)."""
+    import torch
+
+    import paper_2103_05162_gb300 as gb
+
+    algo = gb.ALGO_DENSEBOX if args.algo == "densebox" else gb.ALGO_FDBSCAN
+    X, eps = workload(args.n, args.seed)
+    n = X.shape[0]
+    mps = [int(x) for x in args.sweep_min_pts.split(",")]
+    pts = torch.from_numpy(X).cuda()
+    lab = torch.empty((len(mps), n), dtype=torch.int32, device="cuda")
+
+    def multi():
+        gb.dbscan_run_multi(pts, eps, mps, algo=algo, labels_out=lab)
+
+    def singles():
+        for k, mp in enumerate(mps):
+            gb.dbscan_run(pts, eps, mp, algo=algo, labels_out=lab[k])
+
+    res = {}
+    for name, f in (("multi", multi), ("singles", singles)):
+        for _ in range(max(3, args.warmup)):
+            f()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            f()
+        t1.record()
+        torch.cuda.synchronize()
+        res[name] = t0.elapsed_time(t1) / args.steps
+    print(json.dumps({
+        "metric": "minPts sweep: one index and one counting pass vs one run per minPts",
+        "min_pts": mps, "algo": args.algo, "n": n, "multi_ms": res["multi"], "singles_ms": res["singles"],
+        "speedup": res["singles"] / res["multi"], "value": n * len(mps) / (res["multi"] / 1e3),
+        "unit": "point-clusterings/s", "steps": args.steps,
+        "workload": f"halos3d: {n} 3D float32 points (the benchmark workload), eps={eps:.6g}, minPts in {mps}, "
+                    f"DBSCAN mode"}), flush=True)
+
+
 def _wait_until(target: float) -> float:
     while True:
         now = time.perf_counter()
@@ -507,9 +550,11 @@ def main():
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep"], default="step",
                     help="step: the headline line (default); batch: fused batch vs per-instance runs; "
-                         "serve: Poisson-arrival serving vs sequential runs (1 GPU, rank 0 only)")
+                         "serve: Poisson-arrival serving vs sequential runs; sweep: several minPts over one "
+                         "index vs one run each (these three: 1 GPU, rank 0 only)")
+    ap.add_argument("--sweep-min-pts", default="2,5,10,20")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-algos", default="densebox,fdbscan")
@@ -530,7 +575,7 @@ def main():
         if rank == 0:
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-            (run_batch_mode if args.mode == "batch" else run_serve_mode)(args)
+            {"batch": run_batch_mode, "serve": run_serve_mode, "sweep": run_sweep_mode}[args.mode](args)
         return
     if world > 1:
         import torch

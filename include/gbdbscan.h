@@ -117,6 +117,23 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
                                int algo, int32_t* labels_out, uint8_t* core_out, dbscan_stream stream);
 
 /*
+ * Several minPts over one index (a sweep): for each k < count, writes to
+ * labels_out + k*n (and core_out + k*n if core_out is not NULL) exactly what
+ * dbscan_run(points, n, dim, eps, min_pts[k], mode, algo, ...) writes (core
+ * flags and core labels identical; border labels valid). The index is built
+ * once and the neighbour counts are taken once, stopping at the largest
+ * minPts instead of each one -- the case the paper names as the exception to
+ * early termination (Sec. 3.2); each minPts then runs its own main phase.
+ *   min_pts     host, count values >= 1 (any order, repeats allowed).
+ *   labels_out  device, count*n int32; core_out device, count*n bytes or NULL.
+ * 0 <= count <= 4096; count == 0 or n == 0 returns DBSCAN_OK with no work.
+ * Errors as dbscan_run (checked for every min_pts before any work).
+ */
+dbscan_status dbscan_run_multi(const float* points, int64_t n, int dim, float eps, const int32_t* min_pts,
+                               int32_t count, int mode, int algo, int32_t* labels_out, uint8_t* core_out,
+                               dbscan_stream stream);
+
+/*
  * Serving: a request loop that admits clustering jobs as they arrive, by a
  * device-memory budget and a slot limit, and runs admitted jobs concurrently
  * on their own streams. Jobs keep their device state until collected.

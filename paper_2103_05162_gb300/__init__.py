@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
             "dbscan_run": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_host": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_batch": [vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp],
+            "dbscan_run_multi": [vp, i64, i32, f32, vp, i32, i32, i32, vp, vp, vp],
             "dbscan_server_create": [sz, i32, ctypes.POINTER(vp)],
             "dbscan_server_submit": [vp, vp, i64, i32, f32, i32, i32, i32, vp, vp, ctypes.POINTER(u64)],
             "dbscan_server_poll": [vp, u64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
@@ -153,6 +154,28 @@ def dbscan_run(points, eps: float, min_pts: int, mode="dbscan", algo="densebox",
     with torch.cuda.device(points.device):
         _check(lib.dbscan_run(_ptr(points), n, d, float(eps), int(min_pts), _mode(mode), _algo(algo),
                               _ptr(labels_out), _ptr(core_out), _stream_handle(stream, points.device)))
+    return (labels_out, core_out) if core_out is not None else labels_out
+
+
+def dbscan_run_multi(points, eps: float, min_pts, mode="dbscan", algo="densebox", labels_out=None,
+                     core_out=None, want_core: bool = False, stream=None):
+    """Clusters CUDA ``points`` (n, d) once per value of ``min_pts`` over one
+    index. Returns labels of shape (len(min_pts), n) (and core flags of the
+    same shape if ``want_core`` or ``core_out`` is given); row k is what
+    dbscan_run gives for min_pts[k]."""
+    import torch
+    lib = load()
+    points = points.contiguous()
+    n, d = points.shape
+    mps = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32).reshape(-1))
+    count = int(mps.shape[0])
+    if labels_out is None:
+        labels_out = torch.empty((count, n), dtype=torch.int32, device=points.device)
+    if core_out is None and want_core:
+        core_out = torch.empty((count, n), dtype=torch.uint8, device=points.device)
+    _check(lib.dbscan_run_multi(_ptr(points), n, d, float(eps), ctypes.c_void_p(mps.ctypes.data), count,
+                                _mode(mode), _algo(algo), _ptr(labels_out), _ptr(core_out),
+                                _stream_handle(stream, points.device)))
     return (labels_out, core_out) if core_out is not None else labels_out
 
 

@@ -140,12 +140,19 @@ struct ClusterArgs {
     const int32_t* parent = nullptr;
     const int4* nmeta = nullptr;
     int32_t* tstart = nullptr;
+    // multi-minPts runs: neighbour counts capped at min_pts (null otherwise)
+    int32_t* ncount = nullptr;
 };
 cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s);
 // per-leaf traversal starts (needed by both traversal phases)
 cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s);
-// preprocessing (minPts > 2; nothing otherwise)
+// preprocessing (minPts > 2, or counting for several minPts; nothing otherwise)
 cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s);
+// one minPts of a multi-minPts run: labels and core flags from a.ncount, then
+// border claims from the lists; the caller then runs the main phase with
+// min_pts = max(3, min_pts) (the core flags are exact, so the minPts <= 2
+// forms, which find core points during the main phase, are not needed)
+cudaError_t launch_cluster_from_counts(const ClusterArgs& a, int min_pts, cudaStream_t s);
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
 

@@ -143,6 +143,7 @@ struct Plan {
     uint8_t* nbr;
     int32_t* canon;
     int32_t* nlist;  // n * lcap neighbour indices (preprocessing lists)
+    int32_t* ncount; // n neighbour counts capped at the largest minPts (multi-minPts runs)
 };
 
 int64_t leaf_cap(int64_t n, int algo)
@@ -151,7 +152,7 @@ int64_t leaf_cap(int64_t n, int algo)
     return n;  // tiles hold 1..TILE points, dense cells any number
 }
 
-size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap)
+size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, bool counts = false)
 {
     Carver c(base);
     const int64_t mc = leaf_cap(n, algo);
@@ -192,6 +193,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap)
     p.nbr = c.take<uint8_t>(n);
     p.canon = c.take<int32_t>(n);
     p.nlist = c.take<int32_t>(n * lcap);
+    p.ncount = counts ? c.take<int32_t>(n) : nullptr;
     return c.off + 256;
 }
 
@@ -199,6 +201,12 @@ size_t workspace_bytes(int64_t n, int dim, int algo, int min_pts, int mode)
 {
     Plan p;
     return carve_plan(p, nullptr, n, dim, algo, list_cap(min_pts, mode));
+}
+
+size_t workspace_bytes_multi(int64_t n, int dim, int algo, int max_min_pts, int mode)
+{
+    Plan p;
+    return carve_plan(p, nullptr, n, dim, algo, list_cap(max_min_pts, mode), true);
 }
 
 // ---------------------------------------------------------------------------
@@ -340,16 +348,13 @@ GridParams densebox_grid(const float* lo, const float* hi, int dim, float eps, f
 // the pipeline
 // ---------------------------------------------------------------------------
 enum Stage { ST_BOUNDS, ST_KEYS, ST_SORT, ST_GATHER, ST_LEAVES, ST_LBVH, ST_INIT, ST_PRE, ST_MAIN, ST_FINAL };
-dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
-                           int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
-{
-    const int lcap = list_cap(min_pts, mode);
-    TRY_CUDA(ensure_arena(w->main, workspace_bytes(n, dim, algo, min_pts, mode), s));
-    Plan p;
-    carve_plan(p, w->main.base, n, dim, algo, lcap);
 
-    StageTimer T(w, s);
-    // K1 bounds, then one host wait for them
+// Stages a1-a7: bounds (one host wait for them), keys, sort, gather, leaves
+// (DenseBox cells dense for minPts = dense_mp), BVH. Fills the plan-dependent
+// fields of `a`.
+dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const float* points, int64_t n, int dim,
+                          float eps, int dense_mp, int algo, ClusterArgs& a, cudaStream_t s)
+{
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, 4 * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, 5 * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_M, 0, 2 * sizeof(uint32_t), s));
@@ -381,7 +386,7 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     sb.counters = p.counters;
     sb.err = p.ctrl + CTRL_ERR;
     bool in_alt = false;
-    int64_t m_cap = leaf_cap(n, algo);
+    const int64_t m_cap = leaf_cap(n, algo);
     const uint32_t* perm = nullptr;
 
     if (algo == DBSCAN_ALGO_FDBSCAN) {
@@ -417,7 +422,8 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
         launch_gather(points, perm, n, dim, p.sp, s);
         T.end();
         T.begin(ST_LEAVES);
-        TRY_CUDA(launch_densebox_leaves(keys_sorted, p.sp, n, dim, min_pts, e2, p.db, p.leafr, p.lkey, p.ctrl, s));
+        TRY_CUDA(
+            launch_densebox_leaves(keys_sorted, p.sp, n, dim, dense_mp, e2, p.db, p.leafr, p.lkey, p.ctrl, s));
         T.end();
     }
     TRY_CUDA(cudaGetLastError());
@@ -426,7 +432,6 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     T.end();
     TRY_CUDA(cudaGetLastError());
 
-    ClusterArgs a;
     a.sp = p.sp;
     a.nodes = p.nodes;
     a.nodebox = p.nodebox;
@@ -443,16 +448,31 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     a.core = p.core;
     a.nbr = p.nbr;
     a.nlist = p.nlist;
-    a.lcap = lcap;
     a.canon = p.canon;
     a.ctrl = p.ctrl;
     a.n = n;
     a.m_cap = m_cap;
     a.dim = dim;
     a.e2 = e2;
+    a.block = g_tuning.block;
+    return DBSCAN_OK;
+}
+
+dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                           int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
+{
+    const int lcap = list_cap(min_pts, mode);
+    TRY_CUDA(ensure_arena(w->main, workspace_bytes(n, dim, algo, min_pts, mode), s));
+    Plan p;
+    carve_plan(p, w->main.base, n, dim, algo, lcap);
+
+    StageTimer T(w, s);
+    ClusterArgs a;
+    dbscan_status st = build_index(w, p, T, points, n, dim, eps, min_pts, algo, a, s);
+    if (st != DBSCAN_OK) return st;
     a.min_pts = min_pts;
     a.mode = mode;
-    a.block = g_tuning.block;
+    a.lcap = lcap;
     T.begin(ST_INIT);
     TRY_CUDA(launch_cluster_init(a, s));
     TRY_CUDA(launch_cluster_starts(a, s));
@@ -468,6 +488,56 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     T.begin(ST_FINAL);
     TRY_CUDA(launch_cluster_final(a, labels_out, core_out, s));
     T.end();
+    return DBSCAN_OK;
+}
+
+// Several minPts over one index (the multi-minPts sweep): the tree is built
+// once (DenseBox cells dense for the largest minPts, which makes them dense
+// for every smaller one), preprocessing counts neighbours once with its early
+// exit at the largest minPts (a count capped there decides core for every
+// minPts in the list, and the neighbour lists stay complete for each point
+// that is non-core for some of them), then each minPts takes its own core
+// flags, border claims, main phase and relabel.
+dbscan_status run_multi(Workspace* w, const float* points, int64_t n, int dim, float eps, const int32_t* min_pts,
+                        int count, int mode, int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
+{
+    int max_mp = 1;
+    for (int k = 0; k < count; ++k)
+        if (min_pts[k] > max_mp) max_mp = min_pts[k];
+    const int cap_mp = max_mp < 2 ? 2 : max_mp;  // counting needs at least "a neighbour or not"
+    const int lcap = list_cap(cap_mp, mode);
+    TRY_CUDA(ensure_arena(w->main, workspace_bytes_multi(n, dim, algo, cap_mp, mode), s));
+    Plan p;
+    carve_plan(p, w->main.base, n, dim, algo, lcap, true);
+
+    StageTimer T(w, s);
+    ClusterArgs a;
+    dbscan_status st = build_index(w, p, T, points, n, dim, eps, cap_mp, algo, a, s);
+    if (st != DBSCAN_OK) return st;
+    a.min_pts = cap_mp;
+    a.mode = mode;
+    a.lcap = lcap;
+    a.ncount = p.ncount;
+    T.begin(ST_INIT);
+    TRY_CUDA(cudaMemsetAsync(p.ncount, 0, sizeof(int32_t) * (size_t)n, s));
+    TRY_CUDA(launch_cluster_init(a, s));
+    TRY_CUDA(launch_cluster_starts(a, s));
+    T.end();
+    T.begin(ST_PRE);
+    TRY_CUDA(launch_cluster_pre(a, s));
+    T.end();
+    for (int k = 0; k < count; ++k) {
+        T.begin(ST_MAIN);
+        TRY_CUDA(launch_cluster_from_counts(a, min_pts[k], s));
+        ClusterArgs ak = a;
+        ak.min_pts = min_pts[k] < 3 ? 3 : min_pts[k];
+        TRY_CUDA(launch_cluster_main(ak, s));
+        T.end();
+        T.begin(ST_FINAL);
+        TRY_CUDA(launch_cluster_final(a, labels_out + (size_t)k * n, core_out ? core_out + (size_t)k * n : nullptr,
+                                      s));
+        T.end();
+    }
     return DBSCAN_OK;
 }
 
@@ -511,6 +581,24 @@ dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
     return run_pipeline(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+}
+
+dbscan_status dbscan_run_multi(const float* points, int64_t n, int dim, float eps, const int32_t* min_pts,
+                               int32_t count, int mode, int algo, int32_t* labels_out, uint8_t* core_out,
+                               dbscan_stream stream)
+{
+    t_err.clear();
+    if (count < 0 || count > 4096) return set_error(DBSCAN_ERR_INVALID_ARG, "count must be in [0, 4096]");
+    if (count > 0 && !min_pts) return set_error(DBSCAN_ERR_INVALID_ARG, "null min_pts");
+    for (int32_t k = 0; k < count; ++k) {
+        dbscan_status st = check_run_args(points, n, dim, eps, min_pts[k], mode, algo, labels_out);
+        if (st != DBSCAN_OK) return set_error(st, "min_pts[%d]: %s", k, t_err.c_str());
+    }
+    if (count == 0 || n == 0) return DBSCAN_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    return run_multi(w, points, n, dim, eps, min_pts, count, mode, algo, labels_out, core_out, s);
 }
 
 dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,

@@ -53,8 +53,11 @@ inline int list_cap(int min_pts, int mode)
     return (mode == DBSCAN_MODE_DBSCAN && min_pts > 2 && min_pts <= LIST_MAX_MINPTS) ? min_pts - 1 : 0;
 }
 size_t workspace_bytes(int64_t n, int dim, int algo, int min_pts, int mode);
+size_t workspace_bytes_multi(int64_t n, int dim, int algo, int max_min_pts, int mode);
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
                            int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+dbscan_status run_multi(Workspace* w, const float* points, int64_t n, int dim, float eps, const int32_t* min_pts,
+                        int count, int mode, int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
 // count instances: rows offsets[b]..offsets[b+1]-1 of the concatenation;
 // instance b's points, labels and core flags (cores may be null, or an entry
 // of it) are separate device buffers

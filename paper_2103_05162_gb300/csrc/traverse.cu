@@ -595,6 +595,8 @@ struct DevArgs {
     const int32_t* iroot;
     // per leaf: the node its traversals start at (k_tile_start)
     int32_t* tstart;
+    // multi-minPts runs: neighbour counts capped at min_pts (null otherwise)
+    int32_t* ncount;
 };
 
 template <int D>
@@ -681,7 +683,9 @@ __global__ void k_pre(DevArgs<D> a)
         const int2 r = a.leafr[L];
         if (r.y < 0) continue;  // dense cell: all core already
         const TileParams tp = tile_params(a, L);
-        if (tp.min_pts <= 2) continue;  // Algorithm 3: no preprocessing for minPts <= 2
+        // Algorithm 3: no preprocessing for minPts <= 2 (counts for several
+        // minPts are always taken)
+        if (tp.min_pts <= 2 && !a.ncount) continue;
         const int s = r.x, e = r.y, k = e - s;
         const int q = s + lane;
         // points of dense cells inside the tile are core already
@@ -715,6 +719,7 @@ __global__ void k_pre(DevArgs<D> a)
             // point holds; else whether another point is within eps (the
             // count includes q)
             a.nbr[q] = a.lcap > 0 ? (c ? 0 : (uint8_t)v.nl) : (v.cnt >= 2 ? 1 : 0);
+            if (a.ncount) a.ncount[q] = v.cnt;
         }
     }
 }
@@ -910,6 +915,24 @@ __global__ void __maxnreg__(56) k_main(DevArgs<D> a)
     }
 }
 
+// The same for one minPts of a multi-minPts run, with core flags from the
+// neighbour counts (capped at the largest minPts, which decides every smaller
+// one); points of dense cells are core for every minPts of the run.
+__global__ void k_init_from_counts(const uint8_t* __restrict__ pdense, const int32_t* __restrict__ dstart,
+                                   const int32_t* __restrict__ ncount, int64_t n, int min_pts,
+                                   int32_t* __restrict__ labels, uint8_t* __restrict__ core)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (pdense && pdense[i]) {
+            labels[i] = dstart[i];
+            core[i] = 1;
+        } else {
+            labels[i] = (int32_t)i;
+            core[i] = (min_pts <= 1 || ncount[i] >= min_pts) ? 1 : 0;
+        }
+    }
+}
+
 // labels[i] = i, or the first point of its dense cell (pre-united, Sec. 4.2);
 // core = 1 in dense cells (and everywhere when minPts == 1)
 __global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __restrict__ dstart, int64_t n,
@@ -985,6 +1008,7 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.mps = a.mps;
     d.iroot = a.iroot;
     d.tstart = a.tstart;
+    d.ncount = a.ncount;
     return d;
 }
 
@@ -1039,6 +1063,24 @@ cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_cluster_from_counts(const ClusterArgs& a, int min_pts, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORDS - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
+        cudaSuccess)
+        return e;
+    int64_t gn = (a.n + 255) / 256;
+    if (gn > 152 * 16) gn = 152 * 16;
+    k_init_from_counts<<<(unsigned)gn, 256, 0, s>>>(a.pdense, a.dstart, a.ncount, a.n, min_pts, a.labels, a.core);
+    note_launches(1);
+    if ((e = cudaMemsetAsync(a.canon, 0x7f, sizeof(int32_t) * (size_t)a.n, s)) != cudaSuccess) return e;
+    if (a.lcap > 0 && a.mode == DBSCAN_MODE_DBSCAN) {
+        k_list_claims<<<(unsigned)gn, 256, 0, s>>>(a.nlist, a.lcap, a.nbr, a.core, a.labels, a.n);
+        note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
 {
     int64_t gm = (a.m_cap + 255) / 256;
@@ -1051,13 +1093,15 @@ cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
 
 cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
 {
-    if (a.min_pts <= 2) return cudaSuccess;  // Algorithm 3: no preprocessing for minPts <= 2
+    // Algorithm 3: no preprocessing for minPts <= 2 (counts for several minPts
+    // are always taken)
+    if (a.min_pts <= 2 && !a.ncount) return cudaSuccess;
     cudaError_t e;
     // points that keep no list (instances of a batch with minPts <= 2) read 0
     if (a.lcap > 0 && (e = cudaMemsetAsync(a.nbr, 0, (size_t)a.n, s)) != cudaSuccess) return e;
     if (a.dim == 3) run_pre<3>(a, s); else run_pre<2>(a, s);
     note_launches(1);
-    if (a.lcap > 0) {
+    if (a.lcap > 0 && !a.ncount) {  // (several minPts: claims per minPts)
         int64_t gn = (a.n + 255) / 256;
         if (gn > 152 * 16) gn = 152 * 16;
         k_list_claims<<<(unsigned)gn, 256, 0, s>>>(a.nlist, a.lcap, a.nbr, a.core, a.labels, a.n);

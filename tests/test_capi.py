@@ -100,6 +100,21 @@ def test_batch_argument_errors(lib):
     assert lib.dbscan_run_batch(None, None, None, None, None, 0, 0, 1, None, None, None) == 0
 
 
+def test_multi_argument_errors(lib):
+    P = ctypes.c_void_p(0x1000)
+    mp = np.array([2, 0, 5], dtype=np.int32)
+    st = lib.dbscan_run_multi(P, 10, 3, 0.1, mp.ctypes.data, 3, 0, 1, P, None, None)
+    assert st == 1 and b"min_pts[1]" in lib.dbscan_last_error()
+    mp = np.array([2, 5], dtype=np.int32)
+    assert lib.dbscan_run_multi(P, 10, 4, 0.1, mp.ctypes.data, 2, 0, 1, P, None, None) == 1
+    assert lib.dbscan_run_multi(P, 10, 3, 0.1, None, 2, 0, 1, P, None, None) == 1
+    assert lib.dbscan_run_multi(P, 10, 3, 0.1, mp.ctypes.data, -1, 0, 1, P, None, None) == 1
+    assert lib.dbscan_run_multi(P, 10, 3, 0.1, mp.ctypes.data, 5000, 0, 1, P, None, None) == 1
+    # nothing to do
+    assert lib.dbscan_run_multi(P, 10, 3, 0.1, None, 0, 0, 1, P, None, None) == 0
+    assert lib.dbscan_run_multi(None, 0, 3, 0.1, mp.ctypes.data, 2, 0, 1, None, None, None) == 0
+
+
 def test_server_argument_errors(lib):
     h = ctypes.c_void_p()
     assert lib.dbscan_server_create(0, 4, ctypes.byref(h)) == 1
