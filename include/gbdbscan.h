@@ -68,7 +68,13 @@ typedef enum {
 } dbscan_status;
 
 typedef enum { DBSCAN_MODE_DBSCAN = 0, DBSCAN_MODE_DBSCAN_STAR = 1 } dbscan_mode;
-typedef enum { DBSCAN_ALGO_FDBSCAN = 0, DBSCAN_ALGO_DENSEBOX = 1 } dbscan_algo;
+/* DBSCAN_ALGO_AUTO chooses per call (dbscan_run, dbscan_run_host,
+ * dbscan_run_multi; not batches) from 2048 sample points and the DenseBox
+ * grid (cells of side eps/sqrt(d)): DenseBox when the estimated share of
+ * points in cells of >= minPts points, or the estimated mean number of points
+ * in a point's cell, reaches its threshold (dbscan_set_auto_threshold), else
+ * FDbscan -- DenseBox pays off on data with dense regions (Sec. 5.1, 6). */
+typedef enum { DBSCAN_ALGO_FDBSCAN = 0, DBSCAN_ALGO_DENSEBOX = 1, DBSCAN_ALGO_AUTO = 2 } dbscan_algo;
 
 /* opaque CUDA stream (cudaStream_t) */
 typedef void* dbscan_stream;
@@ -198,6 +204,26 @@ const char* dbscan_last_error(void);
  * (cell side f*eps/sqrt(dim); 0 = default 1). Results do not depend on them.
  */
 dbscan_status dbscan_set_tuning(int block_size, float cell_factor);
+
+/*
+ * Automatic algorithm choice (DBSCAN_ALGO_AUTO) for data of dimension dim
+ * (2 or 3): DenseBox when the estimated share of points in dense cells is at
+ * least dense_fraction (in [0, 1]) or the estimated mean cell occupancy is at
+ * least occupancy (finite, >= 0), else FDbscan. Defaults: 3D 0.005 and 16
+ * (FDbscan's 30-bit Morton grid is coarser than eps there), 2D 0.3 and 16.
+ * Both arguments negative restore the defaults for dim.
+ * DBSCAN_ERR_INVALID_ARG otherwise.
+ */
+dbscan_status dbscan_set_auto_threshold(int dim, float dense_fraction, float occupancy);
+
+/*
+ * The algorithm the last clustering call on `stream` used (DBSCAN_ALGO_FDBSCAN
+ * or DBSCAN_ALGO_DENSEBOX; -1 before any) and, if it was chosen automatically,
+ * the estimates behind the choice in estimates_out[0..1]: the share of points
+ * in dense cells and the mean cell occupancy (both -1 otherwise).
+ * Host-side bookkeeping only: valid once that call has returned.
+ */
+dbscan_status dbscan_last_choice(dbscan_stream stream, int* algo_out, float* estimates_out);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation (not part of the method; for measurement)

@@ -17,16 +17,18 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "DbscanError", "MODE_DBSCAN", "MODE_DBSCAN_STAR", "ALGO_FDBSCAN", "ALGO_DENSEBOX",
-    "load", "library_path", "dbscan_run", "dbscan_run_host", "dbscan_run_batch", "Server",
-    "sort_pairs_u64", "morton_codes", "lbvh_topology", "set_tuning", "stream_status",
-    "release_workspaces", "profile_enable", "profile_collect", "kernel_launches", "last_stats",
+    "DbscanError", "MODE_DBSCAN", "MODE_DBSCAN_STAR", "ALGO_FDBSCAN", "ALGO_DENSEBOX", "ALGO_AUTO",
+    "load", "library_path", "dbscan_run", "dbscan_run_host", "dbscan_run_batch", "dbscan_run_multi", "Server",
+    "sort_pairs_u64", "sort_pairs_u64_noalloc", "morton_codes", "lbvh_topology", "set_tuning",
+    "set_auto_threshold", "last_choice", "stream_status", "release_workspaces", "profile_enable",
+    "profile_collect", "kernel_launches", "last_stats",
 ]
 
 MODE_DBSCAN = 0
 MODE_DBSCAN_STAR = 1
 ALGO_FDBSCAN = 0
 ALGO_DENSEBOX = 1
+ALGO_AUTO = 2
 
 _STATUS = {
     0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NONFINITE", 5: "DEVICE_TIMEOUT", 6: "BUSY",
@@ -34,7 +36,7 @@ _STATUS = {
 }
 
 _MODES = {"dbscan": MODE_DBSCAN, "dbscan*": MODE_DBSCAN_STAR, "dbscan_star": MODE_DBSCAN_STAR}
-_ALGOS = {"fdbscan": ALGO_FDBSCAN, "densebox": ALGO_DENSEBOX}
+_ALGOS = {"fdbscan": ALGO_FDBSCAN, "densebox": ALGO_DENSEBOX, "auto": ALGO_AUTO}
 
 
 class DbscanError(RuntimeError):
@@ -83,6 +85,8 @@ def load(build_if_missing: bool = True):
             "dbscan_stream_status": [vp],
             "dbscan_release_workspaces": [],
             "dbscan_set_tuning": [i32, f32],
+            "dbscan_set_auto_threshold": [i32, f32, f32],
+            "dbscan_last_choice": [vp, ctypes.POINTER(i32), vp],
             "dbscan_sort_pairs_u64": [vp, vp, i64, i32, vp],
             "dbscan_sort_pairs_u64_noalloc": [vp, vp, i64, i32, vp],
             "dbscan_morton_codes": [vp, i64, i32, vp, vp, i32, vp, vp],
@@ -375,6 +379,23 @@ def last_stats(stream=None) -> dict:
 
 def set_tuning(block_size: int = 0, cell_factor: float = 0.0):
     _check(load().dbscan_set_tuning(int(block_size), float(cell_factor)))
+
+
+def set_auto_threshold(dim: int, dense_fraction: float = -1.0, occupancy: float = -1.0):
+    """For data of dimension ``dim``, algo="auto" takes DenseBox when the
+    estimated share of points in dense cells or the estimated mean cell
+    occupancy reaches its threshold (both negative: the defaults)."""
+    _check(load().dbscan_set_auto_threshold(int(dim), float(dense_fraction), float(occupancy)))
+
+
+def last_choice(stream=None):
+    """(algorithm used by the last call on the stream, estimated dense-point
+    share, estimated mean cell occupancy); the estimates are -1 when the
+    algorithm was not chosen automatically."""
+    a = ctypes.c_int()
+    f = (ctypes.c_float * 2)()
+    _check(load().dbscan_last_choice(_stream_handle(stream), ctypes.byref(a), f))
+    return a.value, f[0], f[1]
 
 
 def stream_status(stream=None):

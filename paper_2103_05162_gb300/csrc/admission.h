@@ -23,7 +23,8 @@ struct MergeLimits {
     int batch_jobs = 4096;
 };
 
-// Job: has n (points), mode, algo and bytes (planned single-run workspace).
+// Job: has n (points), mode, algo, mergeable (false: always runs alone) and
+// bytes (planned single-run workspace).
 // batch_bytes(points, jobs): planned workspace of a fused batch.
 // Moves the chosen jobs from queue to group (in queue order) and returns the
 // bytes to reserve for them; returns 0 and leaves both alone if no queued job
@@ -44,7 +45,7 @@ size_t pick_group(std::list<Job*>& queue, std::vector<Job*>& group, size_t used,
     Job* h = *head;
     group.push_back(h);
     size_t bytes = h->bytes;
-    auto small = [&](const Job* j) { return lim.job_points > 0 && j->n <= lim.job_points; };
+    auto small = [&](const Job* j) { return j->mergeable && lim.job_points > 0 && j->n <= lim.job_points; };
     std::vector<typename std::list<Job*>::iterator> take{head};
     if (small(h)) {
         int64_t pts = h->n;

@@ -463,6 +463,8 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
                         const int32_t* dims, const float* eps, const int32_t* min_pts, int32_t* const* labels,
                         uint8_t* const* cores, int mode, int algo, cudaStream_t s)
 {
+    if (algo != DBSCAN_ALGO_FDBSCAN && algo != DBSCAN_ALGO_DENSEBOX)
+        return set_error(DBSCAN_ERR_INVALID_ARG, "batches take an explicit algorithm (FDBSCAN or DENSEBOX)");
     const int64_t n = offsets[count];
     if (n == 0) return DBSCAN_OK;
     int max_mp = 1;

@@ -76,26 +76,117 @@ __global__ void k_morton32(const float* __restrict__ pts, int64_t n, const uint3
 // floor((x_k - lo_k) * inv_h) clamped to [0, cmax_k], Morton-interleaved (or
 // packed axis by axis when `morton` is 0). values = input index.
 template <int D>
+__device__ __forceinline__ uint64_t cell_key(const float* __restrict__ p, const GridParams& g)
+{
+    uint32_t c[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(p[k], g.lo[k]), g.inv_h)), g.cmax[k]);
+    uint64_t key;
+    if (g.morton) {
+        key = interleave<D>(c);
+    } else {
+        key = 0;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) key = (key << g.bits) | c[k];
+    }
+    return key;
+}
+
+template <int D>
 __global__ void k_cellkey(const float* __restrict__ pts, int64_t n, GridParams g, uint64_t* __restrict__ keys,
                           uint32_t* __restrict__ vals)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(pts[i * D + k], g.lo[k]), g.inv_h)), g.cmax[k]);
-        }
-        uint64_t key;
-        if (g.morton) {
-            key = interleave<D>(c);
-        } else {
-            key = 0;
-#pragma unroll
-            for (int k = D - 1; k >= 0; --k) key = (key << g.bits) | c[k];
-        }
-        keys[i] = key;
+        keys[i] = cell_key<D>(pts + i * D, g);
         vals[i] = (uint32_t)i;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Density estimate for the automatic FDbscan / DenseBox choice: the share of
+// points that lie in DenseBox cells holding at least minPts points, from
+// EST_SAMPLES strided sample points. Their cells go into an open-addressing
+// table; one pass over all points counts the points of each sampled cell
+// (per-block shared counters, flushed once); the estimate is the share of
+// samples whose cell reaches minPts. Above 2^22 points the counting pass
+// reads every stride-th point only and scales its counts by the stride (an
+// estimate either way). Keys use at most 63 bits, so the all-ones word marks
+// an empty slot.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long EST_EMPTY = ~0ull;
+
+__device__ __forceinline__ uint32_t est_hash(uint64_t k)
+{
+    return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> 52);  // 12 bits: EST_SLOTS = 4096
+}
+
+template <int D>
+__global__ void k_est_insert(const float* __restrict__ pts, int64_t n, int s, GridParams g,
+                             unsigned long long* __restrict__ table, int32_t* __restrict__ slot)
+{
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        const int64_t i = (int64_t)j * n / s;
+        const unsigned long long key = cell_key<D>(pts + i * D, g);
+        uint32_t h = est_hash(key);
+        slot[j] = -1;
+        for (int probe = 0; probe < EST_SLOTS; ++probe) {  // load <= 1/2: a slot is always found
+            const unsigned long long prev = atomicCAS(&table[h], EST_EMPTY, key);
+            if (prev == EST_EMPTY || prev == key) {
+                slot[j] = (int32_t)h;
+                break;
+            }
+            h = (h + 1) & (EST_SLOTS - 1);
+        }
+    }
+}
+
+template <int D>
+__global__ void k_est_count(const float* __restrict__ pts, int64_t n, int64_t stride, GridParams g,
+                            const unsigned long long* __restrict__ table, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t sc[EST_SLOTS];
+    for (int t = threadIdx.x; t < EST_SLOTS; t += blockDim.x) sc[t] = 0;
+    __syncthreads();
+    const int64_t nc = (n + stride - 1) / stride;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc; j += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = cell_key<D>(pts + j * stride * D, g);
+        uint32_t h = est_hash(key);
+        for (int probe = 0; probe < EST_SLOTS; ++probe) {
+            const unsigned long long k = __ldg(&table[h]);
+            if (k == key) {
+                atomicAdd(&sc[h], 1u);
+                break;
+            }
+            if (k == EST_EMPTY) break;
+            h = (h + 1) & (EST_SLOTS - 1);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < EST_SLOTS; t += blockDim.x)
+        if (sc[t]) atomicAdd(&counts[t], sc[t]);
+}
+
+// out[0] = samples whose cell holds >= min_pts points; out[1..2] = the sum
+// over the samples of their cell's point count (64-bit, low word first)
+__global__ void k_est_result(const int32_t* __restrict__ slot, int s, const uint32_t* __restrict__ counts,
+                             int64_t n, int64_t stride, int min_pts, uint32_t* __restrict__ out)
+{
+    uint32_t c = 0;
+    unsigned long long occ = 0;
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        if (slot[j] < 0) continue;
+        // the sample itself once, the other counted points of its cell scaled
+        // by the stride (the sample is among the counted points iff its index
+        // is a multiple of the stride)
+        const int64_t i = (int64_t)j * n / s;
+        const unsigned long long self = (i % stride == 0) ? 1ull : 0ull;
+        const unsigned long long others = (unsigned long long)counts[slot[j]] - self;
+        const unsigned long long k = 1ull + others * (unsigned long long)stride;
+        if (k >= (unsigned long long)min_pts) ++c;
+        occ += k;
+    }
+    atomicAdd(out, c);
+    atomicAdd(reinterpret_cast<unsigned long long*>(out + 2), occ);
 }
 
 // generic Morton codes with host-side bounds (component entry point)
@@ -391,6 +482,29 @@ __global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, const GridParams& g, int min_pts,
+                                   const EstBuffers& eb, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(eb.table, 0xff, sizeof(unsigned long long) * EST_SLOTS, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(eb.counts, 0, sizeof(uint32_t) * EST_SLOTS, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(eb.result, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    const int smp = n < EST_SAMPLES ? (int)n : EST_SAMPLES;
+    const int64_t stride = n > (int64_t(1) << 22) ? n >> 22 : 1;
+    int64_t gb = (n / stride + 255) / 256;
+    if (gb > 152 * 4) gb = 152 * 4;
+    if (dim == 3) {
+        k_est_insert<3><<<1, 1024, 0, s>>>(points, n, smp, g, eb.table, eb.slot);
+        k_est_count<3><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, eb.table, eb.counts);
+    } else {
+        k_est_insert<2><<<1, 1024, 0, s>>>(points, n, smp, g, eb.table, eb.slot);
+        k_est_count<2><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, eb.table, eb.counts);
+    }
+    k_est_result<<<1, 1024, 0, s>>>(eb.slot, smp, eb.counts, n, stride, min_pts, eb.result);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
 static inline unsigned grid_for(int64_t work, int threads, int max_blocks)
 {
     int64_t b = (work + threads - 1) / threads;

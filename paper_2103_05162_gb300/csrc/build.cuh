@@ -34,6 +34,23 @@ struct GridParams {
     int morton;         // 1: interleave, 0: pack axis by axis
 };
 
+// density estimate (automatic algorithm choice)
+constexpr int EST_SAMPLES = 2048;
+constexpr int EST_SLOTS = 4096;
+struct EstBuffers {
+    unsigned long long* table;  // EST_SLOTS cell keys
+    int32_t* slot;              // EST_SAMPLES: the table slot of each sample's cell
+    uint32_t* counts;           // EST_SLOTS: points per sampled cell
+    uint32_t* result;           // 4 words: [0] samples whose cell holds >= minPts points, [2..3] the
+                                // sum over the samples of their cell's point count (u64, 8-byte aligned)
+};
+// over the samples (min(n, EST_SAMPLES), strided; above 2^22 points the cells
+// are counted on every (n >> 22)-th point, scaled): how many lie in DenseBox
+// cells (grid g) of at least min_pts points, and the summed point counts of
+// their cells (the size-biased mean occupancy once divided by the samples)
+cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, const GridParams& g, int min_pts,
+                                   const EstBuffers& eb, cudaStream_t s);
+
 struct DenseBoxTemps {
     uint8_t* pdense;    // n: 0 not dense, 1 dense cell within a tile, 2 dense cell as its own leaf
     int32_t* dstart;    // n: first point of the dense cell (valid where pdense != 0)

@@ -44,7 +44,10 @@ dbscan_status cuda_error(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_error(e_, #x);   \
     } while (0)
 
-Tuning g_tuning = {128, 1.0f};
+Tuning g_tuning = {128,
+                   1.0f,
+                   {0.0f, 0.0f, DEFAULT_AUTO_FRACTION_2D, DEFAULT_AUTO_FRACTION_3D},
+                   {0.0f, 0.0f, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY}};
 
 // ---------------------------------------------------------------------------
 // launch counting and opt-in per-stage timing (CUDA events on the stream)
@@ -144,6 +147,7 @@ struct Plan {
     int32_t* canon;
     int32_t* nlist;  // n * lcap neighbour indices (preprocessing lists)
     int32_t* ncount; // n neighbour counts capped at the largest minPts (multi-minPts runs)
+    EstBuffers est;  // density estimate (automatic algorithm choice)
 };
 
 int64_t leaf_cap(int64_t n, int algo)
@@ -168,7 +172,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.counters = c.take<uint32_t>(8);
     p.status = c.take<uint32_t>(sort_status_words(n, 8, 64));
     p.sp = c.take<char>(pt * (size_t)n);
-    if (algo == DBSCAN_ALGO_DENSEBOX) {
+    if (algo != DBSCAN_ALGO_FDBSCAN) {  // DenseBox, or possibly (automatic choice)
         p.db.pdense = c.take<uint8_t>(n);
         p.db.dstart = c.take<int32_t>(n);
     } else {
@@ -194,6 +198,10 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.canon = c.take<int32_t>(n);
     p.nlist = c.take<int32_t>(n * lcap);
     p.ncount = counts ? c.take<int32_t>(n) : nullptr;
+    p.est.table = c.take<unsigned long long>(EST_SLOTS);
+    p.est.slot = c.take<int32_t>(EST_SAMPLES);
+    p.est.counts = c.take<uint32_t>(EST_SLOTS);
+    p.est.result = c.take<uint32_t>(4);
     return c.off + 256;
 }
 
@@ -310,7 +318,7 @@ dbscan_status check_run_args(const void* points, int64_t n, int dim, float eps, 
     if (min_pts < 1) return set_error(DBSCAN_ERR_INVALID_ARG, "min_pts must be >= 1 (got %d)", min_pts);
     if (mode != DBSCAN_MODE_DBSCAN && mode != DBSCAN_MODE_DBSCAN_STAR)
         return set_error(DBSCAN_ERR_INVALID_ARG, "unknown mode %d", mode);
-    if (algo != DBSCAN_ALGO_FDBSCAN && algo != DBSCAN_ALGO_DENSEBOX)
+    if (algo != DBSCAN_ALGO_FDBSCAN && algo != DBSCAN_ALGO_DENSEBOX && algo != DBSCAN_ALGO_AUTO)
         return set_error(DBSCAN_ERR_INVALID_ARG, "unknown algo %d", algo);
     if (n > 0 && (!points || !labels_out)) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
     return DBSCAN_OK;
@@ -355,6 +363,9 @@ enum Stage { ST_BOUNDS, ST_KEYS, ST_SORT, ST_GATHER, ST_LEAVES, ST_LBVH, ST_INIT
 dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const float* points, int64_t n, int dim,
                           float eps, int dense_mp, int algo, ClusterArgs& a, cudaStream_t s)
 {
+    w->last_algo = algo;
+    w->last_dense_fraction = -1.0f;
+    w->last_occupancy = -1.0f;
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, 4 * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, 5 * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_M, 0, 2 * sizeof(uint32_t), s));
@@ -377,6 +388,25 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
         hi[k] = ord2f(hc[CTRL_HI + k]);
     }
     const float e2 = eps * eps;
+
+    if (algo == DBSCAN_ALGO_AUTO) {
+        // the share of points in dense cells, from samples (one more host wait)
+        int key_bits = 0;
+        const GridParams g = densebox_grid(lo, hi, dim, eps, g_tuning.cell_factor, &key_bits);
+        TRY_CUDA(launch_density_estimate(points, n, dim, g, dense_mp, p.est, s));
+        TRY_CUDA(cudaMemcpyAsync(w->ctrl_host, p.est.result, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        const uint32_t dense_samples = w->ctrl_host[0];
+        const uint64_t occ_sum = (uint64_t)w->ctrl_host[2] | ((uint64_t)w->ctrl_host[3] << 32);
+        const int samples = n < EST_SAMPLES ? (int)n : EST_SAMPLES;
+        const float frac = (float)dense_samples / (float)samples;
+        const float occ = (float)((double)occ_sum / (double)samples);
+        algo = (frac >= g_tuning.auto_fraction[dim] || occ >= g_tuning.auto_occupancy[dim]) ? DBSCAN_ALGO_DENSEBOX
+                                                                                          : DBSCAN_ALGO_FDBSCAN;
+        w->last_algo = algo;
+        w->last_dense_fraction = frac;
+        w->last_occupancy = occ;
+    }
 
     SortBuffers sb;
     sb.keys_alt = p.keys_alt;
@@ -637,6 +667,8 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
     if (count == 0) return DBSCAN_OK;
     if (!offsets || !dims || !eps || !min_pts) return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer");
     if (offsets[0] != 0) return set_error(DBSCAN_ERR_INVALID_ARG, "offsets[0] must be 0");
+    if (algo == DBSCAN_ALGO_AUTO)
+        return set_error(DBSCAN_ERR_INVALID_ARG, "batches take an explicit algorithm (FDBSCAN or DENSEBOX)");
     int64_t coords = 0;
     for (int32_t b = 0; b < count; ++b) {
         const int64_t nb = offsets[b + 1] - offsets[b];
@@ -732,6 +764,35 @@ dbscan_status dbscan_last_stats(dbscan_stream stream, int64_t* stats_out)
     TRY_CUDA(cudaMemcpy(ctrl, w->main.base, sizeof(ctrl), cudaMemcpyDeviceToHost));
     stats_out[0] = ctrl[CTRL_M];
     stats_out[1] = ctrl[CTRL_NCELLS];
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_last_choice(dbscan_stream stream, int* algo_out, float* estimates_out)
+{
+    t_err.clear();
+    if (!algo_out || !estimates_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null argument");
+    Workspace* w = get_workspace(static_cast<cudaStream_t>(stream));
+    *algo_out = w ? w->last_algo : -1;
+    estimates_out[0] = w ? w->last_dense_fraction : -1.0f;
+    estimates_out[1] = w ? w->last_occupancy : -1.0f;
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_set_auto_threshold(int dim, float dense_fraction, float occupancy)
+{
+    t_err.clear();
+    if (dim != 2 && dim != 3) return set_error(DBSCAN_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", dim);
+    if (dense_fraction < 0.0f && occupancy < 0.0f) {  // restore the defaults
+        g_tuning.auto_fraction[dim] = dim == 2 ? DEFAULT_AUTO_FRACTION_2D : DEFAULT_AUTO_FRACTION_3D;
+        g_tuning.auto_occupancy[dim] = DEFAULT_AUTO_OCCUPANCY;
+        return DBSCAN_OK;
+    }
+    if (!(dense_fraction >= 0.0f && dense_fraction <= 1.0f))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "dense_fraction must be in [0, 1]");
+    if (!(occupancy >= 0.0f) || std::isinf(occupancy))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "occupancy must be finite and >= 0");
+    g_tuning.auto_fraction[dim] = dense_fraction;
+    g_tuning.auto_occupancy[dim] = occupancy;
     return DBSCAN_OK;
 }
 

@@ -28,12 +28,28 @@ struct Workspace {
     // it from and join it back to the caller's stream
     cudaStream_t gstream = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // the algorithm the last run on this stream used, and the dense-point
+    // estimate behind it (-1 when the caller chose the algorithm)
+    int last_algo = -1;
+    float last_dense_fraction = -1.0f;
+    float last_occupancy = -1.0f;
 };
 
 struct Tuning {
-    int block;          // traversal block size (threads)
-    float cell_factor;  // DenseBox cell side factor f in (0, 1]
+    int block;             // traversal block size (threads)
+    float cell_factor;     // DenseBox cell side factor f in (0, 1]
+    // DBSCAN_ALGO_AUTO, per dimension (index 2, 3): DenseBox from this
+    // estimated dense-point share up, or from this estimated mean cell
+    // occupancy up
+    float auto_fraction[4];
+    float auto_occupancy[4];
 };
+// defaults from measurements on GB300: in 3D FDbscan's 10-bit Morton grid is
+// coarser than eps and DenseBox wins as soon as a few dense cells exist; in
+// 2D FDbscan's 16-bit grid is finer than the DenseBox cells and wins unless
+// the data is dense
+constexpr float DEFAULT_AUTO_FRACTION_2D = 0.3f, DEFAULT_AUTO_FRACTION_3D = 0.005f;
+constexpr float DEFAULT_AUTO_OCCUPANCY = 16.0f;
 extern Tuning g_tuning;
 
 dbscan_status set_error(dbscan_status st, const char* fmt, ...);

@@ -13,6 +13,7 @@ struct J {
     int idx;
     long long n;
     int mode, algo;
+    bool mergeable;  // algorithm 2 (automatic choice) never merges
     size_t bytes;
 };
 
@@ -29,6 +30,7 @@ int main()
         unsigned long long b;
         if (scanf("%lld %d %d %llu", &jobs[i].n, &jobs[i].mode, &jobs[i].algo, &b) != 4) return 2;
         jobs[i].idx = i;
+        jobs[i].mergeable = jobs[i].algo != 2;
         jobs[i].bytes = (size_t)b;
         queue.push_back(&jobs[i]);
     }

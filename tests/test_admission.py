@@ -70,6 +70,14 @@ def test_merging_off(driver):
     assert pick(driver, jobs, job_points=0) == (10, [0], [1])
 
 
+def test_automatic_choice_jobs_never_merge(driver):
+    jobs = [(10, 0, 2, 10), (10, 0, 2, 10), (10, 0, 1, 10)]
+    assert pick(driver, jobs) == (10, [0], [1, 2])
+    jobs = [(10, 0, 1, 10), (10, 0, 2, 10), (10, 0, 1, 10)]
+    b, chosen, left = pick(driver, jobs)
+    assert chosen == [0, 2] and left == [1]
+
+
 def test_batch_point_and_job_limits(driver):
     jobs = [(60, 0, 0, 60)] * 6
     b, chosen, left = pick(driver, jobs, batch_points=150)

@@ -85,6 +85,28 @@ def test_tuning_validation(lib):
     assert lib.dbscan_set_tuning(0, 0.0) == 0
 
 
+def test_auto_choice_arguments(lib):
+    assert lib.dbscan_set_auto_threshold(3, -0.1, 16.0) == 1
+    assert lib.dbscan_set_auto_threshold(3, 1.5, 16.0) == 1
+    assert lib.dbscan_set_auto_threshold(3, float("nan"), 16.0) == 1
+    assert lib.dbscan_set_auto_threshold(3, 0.3, -1.0) == 1
+    assert lib.dbscan_set_auto_threshold(3, 0.3, float("inf")) == 1
+    assert lib.dbscan_set_auto_threshold(4, 0.3, 16.0) == 1
+    assert lib.dbscan_set_auto_threshold(2, 0.3, 16.0) == 0
+    assert lib.dbscan_set_auto_threshold(3, -1.0, -1.0) == 0  # defaults
+    assert lib.dbscan_last_choice(None, None, None) == 1
+    # the automatic choice is accepted by single runs, refused by batches
+    P = 0x1000
+    assert _run(lib, P, 10, 4, 0.1, 2, algo=2) == 1 and b"dim" in lib.dbscan_last_error()
+    off = np.array([0, 5], dtype=np.int64)
+    dims = np.array([3], dtype=np.int32)
+    eps = np.array([0.1], dtype=np.float32)
+    mp = np.array([2], dtype=np.int32)
+    st = lib.dbscan_run_batch(ctypes.c_void_p(P), off.ctypes.data, dims.ctypes.data, eps.ctypes.data,
+                              mp.ctypes.data, 1, 0, 2, ctypes.c_void_p(P), None, None)
+    assert st == 1 and b"explicit algorithm" in lib.dbscan_last_error()
+
+
 def test_batch_argument_errors(lib):
     off = np.array([0, 5, 3], dtype=np.int64)
     dims = np.array([3, 3], dtype=np.int32)
