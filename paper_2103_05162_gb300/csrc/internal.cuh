@@ -61,6 +61,59 @@ __device__ __forceinline__ float gap2_rn(float alo, float ahi, float blo, float 
 }
 
 // ---------------------------------------------------------------------------
+// Pairs of fp32 values in one 64-bit register, for the packed f32x2
+// arithmetic of sm_100-family GPUs: each half is rounded to nearest even on
+// its own, so sub2 / add2 / mul2 give exactly __fsub_rn / __fadd_rn /
+// __fmul_rn per half, in half the instructions.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpk2(f32x2 v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sqr2(f32x2 a)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r) : "l"(a));
+    return r;
+}
+// gap_rn per half: max(lo - p, p - hi, 0)
+__device__ __forceinline__ f32x2 gap_rn2(f32x2 lo, f32x2 hi, f32x2 p)
+{
+    float a0, a1, b0, b1;
+    unpk2(sub2(lo, p), a0, a1);
+    unpk2(sub2(p, hi), b0, b1);
+    return pk2(fmaxf(fmaxf(a0, b0), 0.0f), fmaxf(fmaxf(a1, b1), 0.0f));
+}
+// gap2_rn per half, interval [alo, ahi] against the pair of intervals [blo, bhi]
+__device__ __forceinline__ f32x2 gap2_rn2(f32x2 alo, f32x2 ahi, f32x2 blo, f32x2 bhi)
+{
+    float a0, a1, b0, b1;
+    unpk2(sub2(blo, ahi), a0, a1);
+    unpk2(sub2(alo, bhi), b0, b1);
+    return pk2(fmaxf(fmaxf(a0, b0), 0.0f), fmaxf(fmaxf(a1, b1), 0.0f));
+}
+
+// ---------------------------------------------------------------------------
 // Per-dimension storage traits.
 //   Point: sorted coordinates (float4 with w unused in 3D, float2 in 2D).
 //   Box:   an axis-aligned box, 3D (lo.xyz in a, hi.xyz in b) / 2D (lo.xy, hi.xy in a).
@@ -72,7 +125,10 @@ template <int D> struct Traits;
 template <> struct Traits<3> {
     using Point = float4;
     struct Box { float4 lo, hi; };
-    struct Node { float4 a, b, c; int4 m; };  // 64 B
+    // 64 B: per axis (left lo, right lo, left hi, right hi) in a, b, c (x, y,
+    // z), so that one load gives the lo and hi pairs of both children on
+    // that axis; m = (left child, right child, split, last leaf)
+    struct Node { float4 a, b, c; int4 m; };
 
     __device__ static __forceinline__ Point load_point(const float* p, int64_t i)
     {
@@ -140,9 +196,9 @@ template <> struct Traits<3> {
     __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
     {
         Node n;
-        n.a = make_float4(L.lo.x, L.lo.y, L.lo.z, L.hi.x);
-        n.b = make_float4(L.hi.y, L.hi.z, R.lo.x, R.lo.y);
-        n.c = make_float4(R.lo.z, R.hi.x, R.hi.y, R.hi.z);
+        n.a = make_float4(L.lo.x, R.lo.x, L.hi.x, R.hi.x);
+        n.b = make_float4(L.lo.y, R.lo.y, L.hi.y, R.hi.y);
+        n.c = make_float4(L.lo.z, R.lo.z, L.hi.z, R.hi.z);
         n.m = make_int4(left, right, split, last);
         return n;
     }
@@ -151,7 +207,7 @@ template <> struct Traits<3> {
 template <> struct Traits<2> {
     using Point = float2;
     struct Box { float4 lo, hi; };  // z unused
-    struct Node { float4 a, b; int4 m; };  // 48 B
+    struct Node { float4 a, b; int4 m; };  // 48 B: per axis as in 3D (a: x, b: y), then m
 
     __device__ static __forceinline__ Point load_point(const float* p, int64_t i)
     {
@@ -214,8 +270,8 @@ template <> struct Traits<2> {
     __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
     {
         Node n;
-        n.a = make_float4(L.lo.x, L.lo.y, L.hi.x, L.hi.y);
-        n.b = make_float4(R.lo.x, R.lo.y, R.hi.x, R.hi.y);
+        n.a = make_float4(L.lo.x, R.lo.x, L.hi.x, R.hi.x);
+        n.b = make_float4(L.lo.y, R.lo.y, L.hi.y, R.hi.y);
         n.m = make_int4(left, right, split, last);
         return n;
     }

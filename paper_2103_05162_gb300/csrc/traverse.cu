@@ -37,9 +37,13 @@ namespace {
 
 constexpr int STACK = 128;  // > the largest possible tree depth (97 for 64-bit keys + index tie-break)
 
+// Node access and the box tests of both children at once (packed pairs: the
+// left child in the low half, the right child in the high half).
 template <int D> struct NB;
 template <> struct NB<3> {
     using T = Traits<3>;
+    struct PP { f32x2 x, y, z; };  // a point's coordinates, each twice
+    __device__ static __forceinline__ PP pack(const T::Point& p) { return PP{pk2(p.x, p.x), pk2(p.y, p.y), pk2(p.z, p.z)}; }
     __device__ static __forceinline__ T::Node load(const T::Node* n, int i)
     {
         T::Node r;
@@ -48,27 +52,27 @@ template <> struct NB<3> {
     }
     __device__ static __forceinline__ T::Box box_l(const T::Node& n)
     {
-        return T::Box{make_float4(n.a.x, n.a.y, n.a.z, 0.f), make_float4(n.a.w, n.b.x, n.b.y, 0.f)};
+        return T::Box{make_float4(n.a.x, n.b.x, n.c.x, 0.f), make_float4(n.a.z, n.b.z, n.c.z, 0.f)};
     }
     __device__ static __forceinline__ T::Box box_r(const T::Node& n)
     {
-        return T::Box{make_float4(n.b.z, n.b.w, n.c.x, 0.f), make_float4(n.c.y, n.c.z, n.c.w, 0.f)};
+        return T::Box{make_float4(n.a.y, n.b.y, n.c.y, 0.f), make_float4(n.a.w, n.b.w, n.c.w, 0.f)};
     }
-    __device__ static __forceinline__ float pl(const T::Node& n, const T::Point& p)
+    // squared point-to-box distances of both children (box_dist2's order)
+    __device__ static __forceinline__ void pd2(const T::Node& n, const PP& p, float& dl, float& dr)
     {
-        return T::box_dist2(p, n.a.x, n.a.y, n.a.z, n.a.w, n.b.x, n.b.y);
+        f32x2 s = sqr2(gap_rn2(pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w), p.x));
+        s = add2(s, sqr2(gap_rn2(pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w), p.y)));
+        s = add2(s, sqr2(gap_rn2(pk2(n.c.x, n.c.y), pk2(n.c.z, n.c.w), p.z)));
+        unpk2(s, dl, dr);
     }
-    __device__ static __forceinline__ float pr(const T::Node& n, const T::Point& p)
+    // squared box-to-box distances of both children from q (box_box_dist2's order)
+    __device__ static __forceinline__ void bd2(const T::Node& n, const T::Box& q, float& dl, float& dr)
     {
-        return T::box_dist2(p, n.b.z, n.b.w, n.c.x, n.c.y, n.c.z, n.c.w);
-    }
-    __device__ static __forceinline__ float bl(const T::Node& n, const T::Box& q)
-    {
-        return T::box_box_dist2(q, n.a.x, n.a.y, n.a.z, n.a.w, n.b.x, n.b.y);
-    }
-    __device__ static __forceinline__ float br(const T::Node& n, const T::Box& q)
-    {
-        return T::box_box_dist2(q, n.b.z, n.b.w, n.c.x, n.c.y, n.c.z, n.c.w);
+        f32x2 s = sqr2(gap2_rn2(pk2(q.lo.x, q.lo.x), pk2(q.hi.x, q.hi.x), pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w)));
+        s = add2(s, sqr2(gap2_rn2(pk2(q.lo.y, q.lo.y), pk2(q.hi.y, q.hi.y), pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w))));
+        s = add2(s, sqr2(gap2_rn2(pk2(q.lo.z, q.lo.z), pk2(q.hi.z, q.hi.z), pk2(n.c.x, n.c.y), pk2(n.c.z, n.c.w))));
+        unpk2(s, dl, dr);
     }
     __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
     {
@@ -77,6 +81,8 @@ template <> struct NB<3> {
 };
 template <> struct NB<2> {
     using T = Traits<2>;
+    struct PP { f32x2 x, y; };
+    __device__ static __forceinline__ PP pack(const T::Point& p) { return PP{pk2(p.x, p.x), pk2(p.y, p.y)}; }
     __device__ static __forceinline__ T::Node load(const T::Node* n, int i)
     {
         T::Node r;
@@ -85,27 +91,23 @@ template <> struct NB<2> {
     }
     __device__ static __forceinline__ T::Box box_l(const T::Node& n)
     {
-        return T::Box{make_float4(n.a.x, n.a.y, 0.f, 0.f), make_float4(n.a.z, n.a.w, 0.f, 0.f)};
+        return T::Box{make_float4(n.a.x, n.b.x, 0.f, 0.f), make_float4(n.a.z, n.b.z, 0.f, 0.f)};
     }
     __device__ static __forceinline__ T::Box box_r(const T::Node& n)
     {
-        return T::Box{make_float4(n.b.x, n.b.y, 0.f, 0.f), make_float4(n.b.z, n.b.w, 0.f, 0.f)};
+        return T::Box{make_float4(n.a.y, n.b.y, 0.f, 0.f), make_float4(n.a.w, n.b.w, 0.f, 0.f)};
     }
-    __device__ static __forceinline__ float pl(const T::Node& n, const T::Point& p)
+    __device__ static __forceinline__ void pd2(const T::Node& n, const PP& p, float& dl, float& dr)
     {
-        return T::box_dist2(p, n.a.x, n.a.y, n.a.z, n.a.w);
+        f32x2 s = sqr2(gap_rn2(pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w), p.x));
+        s = add2(s, sqr2(gap_rn2(pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w), p.y)));
+        unpk2(s, dl, dr);
     }
-    __device__ static __forceinline__ float pr(const T::Node& n, const T::Point& p)
+    __device__ static __forceinline__ void bd2(const T::Node& n, const T::Box& q, float& dl, float& dr)
     {
-        return T::box_dist2(p, n.b.x, n.b.y, n.b.z, n.b.w);
-    }
-    __device__ static __forceinline__ float bl(const T::Node& n, const T::Box& q)
-    {
-        return T::box_box_dist2(q, n.a.x, n.a.y, n.a.z, n.a.w);
-    }
-    __device__ static __forceinline__ float br(const T::Node& n, const T::Box& q)
-    {
-        return T::box_box_dist2(q, n.b.x, n.b.y, n.b.z, n.b.w);
+        f32x2 s = sqr2(gap2_rn2(pk2(q.lo.x, q.lo.x), pk2(q.hi.x, q.hi.x), pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w)));
+        s = add2(s, sqr2(gap2_rn2(pk2(q.lo.y, q.lo.y), pk2(q.hi.y, q.hi.y), pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w))));
+        unpk2(s, dl, dr);
     }
     __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
     {
@@ -113,8 +115,42 @@ template <> struct NB<2> {
     }
 };
 
+// Up to 32 staged points by coordinate (structure of arrays): two
+// neighbouring points load as one packed pair per axis.
+template <int D> struct SoA;
+template <> struct __align__(16) SoA<3> {
+    float x[32], y[32], z[32];
+    __device__ __forceinline__ void put(int l, const float4& p) { x[l] = p.x; y[l] = p.y; z[l] = p.z; }
+    // dist2(p, point u) and dist2(p, point u + 1) for even u (p packed)
+    __device__ __forceinline__ void d2pair(const NB<3>::PP& p, int u, float& d0, float& d1) const
+    {
+        const f32x2 bx = *reinterpret_cast<const f32x2*>(&x[u]);
+        const f32x2 by = *reinterpret_cast<const f32x2*>(&y[u]);
+        const f32x2 bz = *reinterpret_cast<const f32x2*>(&z[u]);
+        f32x2 s = sqr2(sub2(p.x, bx));
+        s = add2(s, sqr2(sub2(p.y, by)));
+        s = add2(s, sqr2(sub2(p.z, bz)));
+        unpk2(s, d0, d1);
+    }
+    __device__ __forceinline__ float d2(const float4& p, int u) const { return dist2(p, make_float4(x[u], y[u], z[u], 0.f)); }
+};
+template <> struct __align__(16) SoA<2> {
+    float x[32], y[32];
+    __device__ __forceinline__ void put(int l, const float2& p) { x[l] = p.x; y[l] = p.y; }
+    __device__ __forceinline__ void d2pair(const NB<2>::PP& p, int u, float& d0, float& d1) const
+    {
+        const f32x2 bx = *reinterpret_cast<const f32x2*>(&x[u]);
+        const f32x2 by = *reinterpret_cast<const f32x2*>(&y[u]);
+        f32x2 s = sqr2(sub2(p.x, bx));
+        s = add2(s, sqr2(sub2(p.y, by)));
+        unpk2(s, d0, d1);
+    }
+    __device__ __forceinline__ float d2(const float2& p, int u) const { return dist2(p, make_float2(x[u], y[u])); }
+};
+
 template <int D>
 struct WarpMem {
+    SoA<D> soa;
     typename Traits<D>::Point buf[32];
     int stack[STACK];
     uint8_t cbuf[32];
@@ -148,9 +184,10 @@ __device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restr
             return;
         }
         const auto nd = NB<D>::load(nodes, node);
-        unsigned ml = 0, mr = 0;
-        if (nd.m.z >= v.mask_lo) ml = __ballot_sync(FULL, v.hit_l(nd));
-        if (nd.m.w >= v.mask_lo) mr = __ballot_sync(FULL, v.hit_r(nd));
+        bool hl, hr;
+        v.hits(nd, hl, hr);
+        const unsigned ml = nd.m.z >= v.mask_lo ? __ballot_sync(FULL, hl) : 0u;
+        const unsigned mr = nd.m.w >= v.mask_lo ? __ballot_sync(FULL, hr) : 0u;
         int next = -1;
         // left child, then right child; one call site of v.leaf keeps the
         // kernel's code small
@@ -190,7 +227,7 @@ struct PreV {
     using P = typename T::Point;
     const P* __restrict__ sp;
     const int2* __restrict__ leafr;
-    P* buf;
+    SoA<D>* soa;
     float e2;
     int min_pts;
     int mask_lo;
@@ -213,8 +250,15 @@ struct PreV {
         ++nl;
     }
 
-    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return act && NB<D>::pl(n, p) <= e2; }
-    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return act && NB<D>::pr(n, p) <= e2; }
+    typename NB<D>::PP pp;  // p, packed
+
+    __device__ __forceinline__ void hits(const typename T::Node& n, bool& hl, bool& hr) const
+    {
+        float dl, dr;
+        NB<D>::pd2(n, pp, dl, dr);
+        hl = act && dl <= e2;
+        hr = act && dr <= e2;
+    }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, act); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -256,18 +300,27 @@ struct PreV {
                     }
                 }
             } else {
-                // lane per query, looping over the staged leaf points
-                if (lane < k) buf[lane] = sp[c + lane];
+                // lane per query, looping over the staged leaf points two
+                // at a time (packed); a count that reaches minPts stops
+                if (lane < k) soa->put(lane, sp[c + lane]);
                 __syncwarp();
                 if ((mask >> lane) & 1u) {
-                    for (int u = 0; u < k; ++u) {
-                        if (dist2(p, buf[u]) <= e2) {
+                    int u = 0;
+                    for (; u + 1 < k && act; u += 2) {
+                        float d0, d1;
+                        soa->d2pair(pp, u, d0, d1);
+                        if (d0 <= e2) {
                             if (nlist) note(c + u);
-                            if (++cnt >= min_pts) {
-                                act = false;
-                                break;
-                            }
+                            if (++cnt >= min_pts) act = false;
                         }
+                        if (d1 <= e2 && act) {
+                            if (nlist) note(c + u + 1);
+                            if (++cnt >= min_pts) act = false;
+                        }
+                    }
+                    if (u < k && act && soa->d2(p, u) <= e2) {
+                        if (nlist) note(c + u);
+                        if (++cnt >= min_pts) act = false;
                     }
                 }
                 __syncwarp();
@@ -351,8 +404,15 @@ struct MainPtV {
     bool qcore;
     int last = -1;  // pair_memo state of this lane's query
 
-    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return valid && NB<D>::pl(n, p) <= e2; }
-    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return valid && NB<D>::pr(n, p) <= e2; }
+    typename NB<D>::PP pp;  // p, packed
+
+    __device__ __forceinline__ void hits(const typename T::Node& n, bool& hl, bool& hr) const
+    {
+        float dl, dr;
+        NB<D>::pd2(n, pp, dl, dr);
+        hl = valid && dl <= e2;
+        hr = valid && dr <= e2;
+    }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -431,8 +491,15 @@ struct MainSolidV {
     bool valid;
     typename T::Box qb;
 
-    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return valid && NB<D>::pl(n, p) <= e2; }
-    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return valid && NB<D>::pr(n, p) <= e2; }
+    typename NB<D>::PP pp;  // p, packed
+
+    __device__ __forceinline__ void hits(const typename T::Node& n, bool& hl, bool& hr) const
+    {
+        float dl, dr;
+        NB<D>::pd2(n, pp, dl, dr);
+        hl = valid && dl <= e2;
+        hr = valid && dr <= e2;
+    }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -511,8 +578,13 @@ struct MainBoxV {
     int sQ, eQ;
     typename T::Box qb;
 
-    __device__ __forceinline__ bool hit_l(const typename T::Node& n) const { return NB<D>::bl(n, qb) <= e2; }
-    __device__ __forceinline__ bool hit_r(const typename T::Node& n) const { return NB<D>::br(n, qb) <= e2; }
+    __device__ __forceinline__ void hits(const typename T::Node& n, bool& hl, bool& hr) const
+    {
+        float dl, dr;
+        NB<D>::bd2(n, qb, dl, dr);
+        hl = dl <= e2;
+        hr = dr <= e2;
+    }
     __device__ __forceinline__ unsigned root_mask() const { return FULL; }
 
     __device__ bool leaf(int L, unsigned, const typename T::Box& box)
@@ -670,8 +742,9 @@ __device__ __forceinline__ int next_leaf(uint32_t* ctr)
     return __shfl_sync(FULL, L, 0);
 }
 
+// (56 registers: nine 128-thread blocks per SM)
 template <int D>
-__global__ void k_pre(DevArgs<D> a)
+__global__ void __maxnreg__(56) k_pre(DevArgs<D> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
@@ -693,19 +766,27 @@ __global__ void k_pre(DevArgs<D> a)
         if (!__any_sync(FULL, counts)) continue;
         const typename Traits<D>::Point p = a.sp[q < e ? q : s];
         // the tile's own points first: in dense regions most queries reach
-        // minPts here and need no traversal at all
-        wm->buf[lane] = p;
+        // minPts here and need no traversal at all (two points at a time)
+        wm->soa.put(lane, p);
         __syncwarp();
+        const typename NB<D>::PP pp = NB<D>::pack(p);
         int cnt = 0;
-        if (counts)
-            for (int u = 0; u < k; ++u)
-                if (dist2(p, wm->buf[u]) <= tp.e2 && ++cnt >= tp.min_pts) break;
+        if (counts) {
+            int u = 0;
+            for (; u + 1 < k && cnt < tp.min_pts; u += 2) {
+                float d0, d1;
+                wm->soa.d2pair(pp, u, d0, d1);
+                cnt += (d0 <= tp.e2) + (d1 <= tp.e2);
+            }
+            if (u < k && cnt < tp.min_pts && wm->soa.d2(p, u) <= tp.e2) ++cnt;
+        }
         __syncwarp();
         PreV<D> v;
-        v.sp = a.sp; v.leafr = a.leafr; v.buf = wm->buf; v.e2 = tp.e2; v.min_pts = tp.min_pts;
+        v.sp = a.sp; v.leafr = a.leafr; v.soa = &wm->soa; v.e2 = tp.e2; v.min_pts = tp.min_pts;
         v.mask_lo = 0; v.own = L; v.lane = lane;
         v.act = counts && cnt < tp.min_pts;
         v.p = p;
+        v.pp = pp;
         v.cnt = cnt;
         v.nlist = a.lcap > 0 ? a.nlist : nullptr;
         v.lcap = a.lcap;
@@ -894,6 +975,7 @@ __global__ void __maxnreg__(56) k_main(DevArgs<D> a)
             // from their lists and need no traversal)
             v.valid = in && (tp.min_pts <= 2 || v.qcore || (rule.claims && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
+            v.pp = NB<D>::pack(v.p);
             if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
         } else if (KIND == 1) {
             MainSolidV<D> v;
@@ -901,6 +983,7 @@ __global__ void __maxnreg__(56) k_main(DevArgs<D> a)
             v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
             v.valid = s + lane < e;
             v.p = a.sp[v.valid ? s + lane : s];
+            v.pp = NB<D>::pack(v.p);
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
             traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
