@@ -391,7 +391,7 @@ struct MainPtV {
     const int2* __restrict__ leafr;
     const uint8_t* __restrict__ lsolid;
     const uint8_t* core;
-    P* buf;
+    SoA<D>* soa;
     uint8_t* cbuf;
     Rule rule;
     float e2;
@@ -440,11 +440,23 @@ struct MainPtV {
                     __syncwarp();
                 }
             } else {
-                if (lane < k) { buf[lane] = sp[s + lane]; cbuf[lane] = core[s + lane]; }
+                if (lane < k) { soa->put(lane, sp[s + lane]); cbuf[lane] = core[s + lane]; }
                 __syncwarp();
-                if ((mask >> lane) & 1u)
-                    for (int u = 0; u < k; ++u)
-                        if (cont || dist2(p, buf[u]) <= e2) rule.pair_memo(q, qcore, s + u, cbuf[u] != 0, last);
+                if ((mask >> lane) & 1u) {
+                    if (cont) {
+                        for (int u = 0; u < k; ++u) rule.pair_memo(q, qcore, s + u, cbuf[u] != 0, last);
+                    } else {
+                        // two staged points at a time (packed)
+                        int u = 0;
+                        for (; u + 1 < k; u += 2) {
+                            float d0, d1;
+                            soa->d2pair(pp, u, d0, d1);
+                            if (d0 <= e2) rule.pair_memo(q, qcore, s + u, cbuf[u] != 0, last);
+                            if (d1 <= e2) rule.pair_memo(q, qcore, s + u + 1, cbuf[u + 1] != 0, last);
+                        }
+                        if (u < k && soa->d2(p, u) <= e2) rule.pair_memo(q, qcore, s + u, cbuf[u] != 0, last);
+                    }
+                }
                 __syncwarp();
             }
             return false;
@@ -835,10 +847,14 @@ __global__ void k_list_claims(const int32_t* __restrict__ nlist, int lcap, const
 // neighbour in the tile claims it. Finally the tile records whether it is
 // solid: all points core and in one set. Dense cells larger than a tile are
 // solid by construction.
+constexpr int INTRA_THREADS = 256;
+
 template <int D>
-__global__ void k_intra(DevArgs<D> a)
+__global__ void __launch_bounds__(INTRA_THREADS) k_intra(DevArgs<D> a)
 {
     using P = typename Traits<D>::Point;
+    __shared__ SoA<D> soa_s[INTRA_THREADS / 32];
+    SoA<D>& soa = soa_s[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int64_t m = a.ctrl[CTRL_M];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -853,11 +869,23 @@ __global__ void k_intra(DevArgs<D> a)
         const TileParams tp = tile_params(a, (int)L);
         const bool valid = lane < k;
         const P p = a.sp[valid ? s + lane : s];
+        // the tile's adjacency, two points at a time (packed)
+        soa.put(lane, p);
+        __syncwarp();
         unsigned adj = 0;
-        for (int j = 0; j < k; ++j) {
-            const P pj = NB<D>::shfl(p, j);
-            if (valid && j != lane && dist2(p, pj) <= tp.e2) adj |= 1u << j;
+        if (valid) {
+            const typename NB<D>::PP pp = NB<D>::pack(p);
+            int j = 0;
+            for (; j + 1 < k; j += 2) {
+                float d0, d1;
+                soa.d2pair(pp, j, d0, d1);
+                adj |= (d0 <= tp.e2 ? 1u : 0u) << j;
+                adj |= (d1 <= tp.e2 ? 2u : 0u) << j;
+            }
+            if (j < k && soa.d2(p, j) <= tp.e2) adj |= 1u << j;
+            adj &= ~(1u << lane);
         }
+        __syncwarp();
         bool c = valid && a.core[s + lane];
         if (tp.min_pts == 2) {
             // no preprocessing: a neighbour inside the tile makes a point core
@@ -964,7 +992,7 @@ __global__ void __maxnreg__(56) k_main(DevArgs<D> a)
         const int s = r.x, e = r.y & 0x7fffffff;
         if (KIND == 0) {
             MainPtV<D> v;
-            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
+            v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.soa = &wm->soa;
             v.cbuf = wm->cbuf; v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
             v.q = s + lane;
             const bool in = v.q < e;
@@ -1118,9 +1146,9 @@ void run_main_kind(const ClusterArgs& a, cudaStream_t s)
 template <int D>
 void run_main(const ClusterArgs& a, cudaStream_t s)
 {
-    int64_t gw = (a.m_cap * 32 + 255) / 256;
+    int64_t gw = (a.m_cap * 32 + INTRA_THREADS - 1) / INTRA_THREADS;
     if (gw > 152 * 16) gw = 152 * 16;
-    k_intra<D><<<(unsigned)gw, 256, 0, s>>>(dev_args<D>(a));
+    k_intra<D><<<(unsigned)gw, INTRA_THREADS, 0, s>>>(dev_args<D>(a));
     int64_t gk = (a.m_cap + 255) / 256;
     if (gk > 152 * 8) gk = 152 * 8;
     k_kinds_count<<<(unsigned)gk, 256, 0, s>>>(a.leafr, a.lsolid, a.ctrl);
