@@ -215,9 +215,13 @@ __global__ void k_bfinalize(int32_t* labels, const uint8_t* __restrict__ core, c
                             const uint64_t* __restrict__ keys, int lb, const InstDev* __restrict__ inst, int64_t n,
                             int32_t* __restrict__ canon)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = uf_find(labels, (int)i);
-        if (core[i]) atomicMin(&canon[r], (int32_t)((int64_t)perm[i] - inst[keys[i] >> lb].off));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + (threadIdx.x & 31);
+        const bool in = i < n;
+        const int r = in ? uf_find(labels, (int)i) : 0;
+        const int32_t v = in ? (int32_t)((int64_t)perm[i] - inst[keys[i] >> lb].off) : 0;
+        warp_atomic_min(canon, r, v, in && core[i]);
     }
 }
 

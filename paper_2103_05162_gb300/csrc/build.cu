@@ -461,9 +461,9 @@ __global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__
                 atomicOr(&ctrl_err[0], ERR_STACK);
                 break;
             }
-            __threadfence();
-            if (atomicAdd(&visit[p], 1) == 0) break;
-            __threadfence();
+            // the first of the two children to arrive stops; the second one
+            // sees the first one's box (release / acquire on the counter)
+            if (atomic_add_acq_rel(&visit[p], 1) == 0) break;
             const int4 mt = nmeta[p];
             Box L, R;
             L.lo = __ldcg(&nodebox[mt.x].lo); L.hi = __ldcg(&nodebox[mt.x].hi);

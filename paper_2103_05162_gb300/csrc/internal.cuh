@@ -330,6 +330,29 @@ __device__ __forceinline__ void uf_claim(int* L, int y, int x)
     atomicCAS(L + y, y, r);
 }
 
+// atomicMin(&a[key], v) for the lanes of the warp that are `active`, with the
+// lanes that share a key combined first: one atomic per distinct key (the
+// canonical-label minimum, where every core point of a large cluster would
+// otherwise hit the same word). All 32 lanes must call it.
+__device__ __forceinline__ void warp_atomic_min(int32_t* a, int key, int32_t v, bool active)
+{
+    const unsigned act = __ballot_sync(FULL, active);
+    if (!active) return;
+    const unsigned peers = __match_any_sync(act, key);
+    const int32_t m = __reduce_min_sync(peers, v);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(a + key, m);
+}
+
+// atomic add with acquire-release ordering at GPU scope: the writes before
+// it are visible to a thread that reads the result, and the reads after it
+// see what the threads before it wrote (in place of a fence on each side)
+__device__ __forceinline__ int atomic_add_acq_rel(int32_t* p, int v)
+{
+    int r;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+    return r;
+}
+
 // relaxed global loads/stores for look-back status words
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p)
 {

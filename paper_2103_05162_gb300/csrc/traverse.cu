@@ -1064,9 +1064,13 @@ __global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __rest
 __global__ void k_finalize(int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
                            int64_t n, int32_t* __restrict__ canon)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = uf_find(labels, (int)i);
-        if (core[i]) atomicMin(&canon[r], (int32_t)perm[i]);
+    // warp-uniform trip count: warp_atomic_min needs all 32 lanes
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + (threadIdx.x & 31);
+        const bool in = i < n;
+        const int r = in ? uf_find(labels, (int)i) : 0;
+        warp_atomic_min(canon, r, in ? (int32_t)perm[i] : 0, in && core[i]);
     }
 }
 
