@@ -287,6 +287,8 @@ struct BatchPlan {
     uint8_t* lsolid;
     int32_t* klist;
     int32_t* tstart;
+    int2* tsib;
+    int8_t* tnsib;
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
@@ -333,6 +335,8 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo, int
     p.lsolid = c.take<uint8_t>(n);
     p.klist = c.take<int32_t>(n);
     p.tstart = c.take<int32_t>(n);
+    p.tsib = c.take<int2>(n * TRAVERSAL_SIBCAP);
+    p.tnsib = c.take<int8_t>(n);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
@@ -428,6 +432,8 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     a.lsolid = p.lsolid;
     a.klist = p.klist;
     a.tstart = p.tstart;
+    a.tsib = p.tsib;
+    a.tnsib = p.tnsib;
     a.parent = p.parent;
     a.nmeta = p.nmeta;
     a.pdense = p.db.pdense;

@@ -120,6 +120,8 @@ void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* p
                         int2* range_out, cudaStream_t s);
 
 // traverse.cu
+constexpr int TRAVERSAL_SIBCAP = 8;  // sibling subtrees recorded per leaf
+
 struct ClusterArgs {
     const void* sp;        // sorted points
     const void* nodes;     // m-1 node records
@@ -157,6 +159,8 @@ struct ClusterArgs {
     const int32_t* parent = nullptr;
     const int4* nmeta = nullptr;
     int32_t* tstart = nullptr;
+    int2* tsib = nullptr;    // m_cap * TRAVERSAL_SIBCAP: (node, last leaf) of the sibling subtrees within eps
+    int8_t* tnsib = nullptr; // m_cap: how many (-1: more than TRAVERSAL_SIBCAP, use tstart)
     // multi-minPts runs: neighbour counts capped at min_pts (null otherwise)
     int32_t* ncount = nullptr;
 };

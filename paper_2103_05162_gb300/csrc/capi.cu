@@ -141,6 +141,8 @@ struct Plan {
     uint8_t* lsolid;
     int32_t* klist;
     int32_t* tstart;
+    int2* tsib;
+    int8_t* tnsib;
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
@@ -192,6 +194,8 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.lsolid = c.take<uint8_t>(mc);
     p.klist = c.take<int32_t>(mc);
     p.tstart = c.take<int32_t>(mc);
+    p.tsib = c.take<int2>(mc * TRAVERSAL_SIBCAP);
+    p.tnsib = c.take<int8_t>(mc);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
@@ -469,6 +473,8 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     a.lsolid = p.lsolid;
     a.klist = p.klist;
     a.tstart = p.tstart;
+    a.tsib = p.tsib;
+    a.tnsib = p.tnsib;
     a.parent = p.parent;
     a.nmeta = p.nmeta;
     a.pdense = algo == DBSCAN_ALGO_DENSEBOX ? p.db.pdense : nullptr;

@@ -74,6 +74,14 @@ template <> struct NB<3> {
         s = add2(s, sqr2(gap2_rn2(pk2(q.lo.z, q.lo.z), pk2(q.hi.z, q.hi.z), pk2(n.c.x, n.c.y), pk2(n.c.z, n.c.w))));
         unpk2(s, dl, dr);
     }
+    __device__ static __forceinline__ float pbox(const T::Point& p, const T::Box& b)
+    {
+        return T::box_dist2(p, b.lo.x, b.lo.y, b.lo.z, b.hi.x, b.hi.y, b.hi.z);
+    }
+    __device__ static __forceinline__ float bbox(const T::Box& q, const T::Box& b)
+    {
+        return T::box_box_dist2(q, b.lo.x, b.lo.y, b.lo.z, b.hi.x, b.hi.y, b.hi.z);
+    }
     __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
     {
         return make_float4(__shfl_sync(FULL, p.x, src), __shfl_sync(FULL, p.y, src), __shfl_sync(FULL, p.z, src), 0.f);
@@ -108,6 +116,14 @@ template <> struct NB<2> {
         f32x2 s = sqr2(gap2_rn2(pk2(q.lo.x, q.lo.x), pk2(q.hi.x, q.hi.x), pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w)));
         s = add2(s, sqr2(gap2_rn2(pk2(q.lo.y, q.lo.y), pk2(q.hi.y, q.hi.y), pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w))));
         unpk2(s, dl, dr);
+    }
+    __device__ static __forceinline__ float pbox(const T::Point& p, const T::Box& b)
+    {
+        return T::box_dist2(p, b.lo.x, b.lo.y, b.hi.x, b.hi.y);
+    }
+    __device__ static __forceinline__ float bbox(const T::Box& q, const T::Box& b)
+    {
+        return T::box_box_dist2(q, b.lo.x, b.lo.y, b.hi.x, b.hi.y);
     }
     __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
     {
@@ -156,25 +172,16 @@ struct WarpMem {
     uint8_t cbuf[32];
 };
 
-// Warp-cooperative stack traversal. Children whose last leaf is below
+// Warp-cooperative stack traversal from internal node `node` with sp
+// entries already on the stack. Children whose last leaf is below
 // v.mask_lo are never entered (the pair mask). v.leaf(L, mask, box) gets the
 // lanes that reached leaf L and its box; it returns true to stop early.
 template <int D, class V>
-__device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes,
-                                         const typename Traits<D>::Box* __restrict__ nodebox, int64_t m, V& v,
-                                         int* stack, uint32_t* ctrl, int start)
+__device__ __forceinline__ void traverse_loop(const typename Traits<D>::Node* __restrict__ nodes, int64_t m, V& v,
+                                              int* stack, uint32_t* ctrl, int node, int sp)
 {
     const int lane = threadIdx.x & 31;
     const int leaf0 = (int)(m - 1);
-    if (start >= leaf0) {
-        // the (sub)tree is a single leaf
-        typename Traits<D>::Box b;
-        b.lo = nodebox[start].lo;
-        b.hi = nodebox[start].hi;
-        v.leaf(start - leaf0, v.root_mask(), b);
-        return;
-    }
-    int node = start, sp = 0;
     // a traversal enters each internal node at most once; more steps than
     // that can only come from a corrupt tree: flag it and stop
     int64_t steps = 0;
@@ -218,6 +225,63 @@ __device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restr
     }
 }
 
+// The traversal of one leaf's points from node `start` (an internal node,
+// or the leaf itself when it is a whole tree).
+template <int D, class V>
+__device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes,
+                                         const typename Traits<D>::Box* __restrict__ nodebox, int64_t m, V& v,
+                                         int* stack, uint32_t* ctrl, int start)
+{
+    const int leaf0 = (int)(m - 1);
+    if (start >= leaf0) {
+        typename Traits<D>::Box b;
+        b.lo = nodebox[start].lo;
+        b.hi = nodebox[start].hi;
+        v.leaf(start - leaf0, v.root_mask(), b);
+        return;
+    }
+    traverse_loop<D>(nodes, m, v, stack, ctrl, start, 0);
+}
+
+// The traversal of one leaf's points from the subtrees roots[0 .. n) (node,
+// last leaf): the siblings along the leaf's path to its start node whose
+// boxes come within eps of the leaf box. Every neighbour of the leaf's points
+// outside the leaf lies in one of them (k_tile_start), so the path nodes
+// themselves are not visited. Roots whose leaves all precede v.mask_lo are
+// skipped; leaf roots are tested lane by lane against their box.
+template <int D, class V>
+__device__ __forceinline__ void traverse_roots(const typename Traits<D>::Node* __restrict__ nodes,
+                                               const typename Traits<D>::Box* __restrict__ nodebox, int64_t m,
+                                               V& v, int* stack, uint32_t* ctrl, const int2* __restrict__ roots,
+                                               int n)
+{
+    const int lane = threadIdx.x & 31;
+    const int leaf0 = (int)(m - 1);
+    int sp = 0;
+    for (int j = n - 1; j >= 0; --j) {  // pushed in reverse: the nearest sibling is taken first
+        const int2 r = roots[j];
+        if (r.y < v.mask_lo) continue;
+        if (r.x >= leaf0) {
+            typename Traits<D>::Box b;
+            b.lo = nodebox[r.x].lo;
+            b.hi = nodebox[r.x].hi;
+            const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+            if (mk && v.leaf(r.x - leaf0, mk, b)) return;
+        } else {
+            if (lane == 0) stack[sp] = r.x;
+            ++sp;
+        }
+    }
+    if (sp == 0) return;
+    __syncwarp();
+    const int node = stack[--sp];
+    traverse_loop<D>(nodes, m, v, stack, ctrl, node, sp);
+}
+
+// per leaf: at most SIBCAP sibling subtrees are recorded (more: the start
+// node is used instead)
+constexpr int SIBCAP = TRAVERSAL_SIBCAP;
+
 // ---------------------------------------------------------------------------
 // Preprocessing visitor: count neighbours up to minPts (Sec. 3.2, 4.1, 4.2).
 // ---------------------------------------------------------------------------
@@ -259,6 +323,7 @@ struct PreV {
         hl = act && dl <= e2;
         hr = act && dr <= e2;
     }
+    __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return act && NB<D>::pbox(p, b) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, act); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -413,6 +478,7 @@ struct MainPtV {
         hl = valid && dl <= e2;
         hr = valid && dr <= e2;
     }
+    __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return valid && NB<D>::pbox(p, b) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -512,6 +578,7 @@ struct MainSolidV {
         hl = valid && dl <= e2;
         hr = valid && dr <= e2;
     }
+    __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return valid && NB<D>::pbox(p, b) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -597,6 +664,7 @@ struct MainBoxV {
         hl = dl <= e2;
         hr = dr <= e2;
     }
+    __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return NB<D>::bbox(qb, b) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return FULL; }
 
     __device__ bool leaf(int L, unsigned, const typename T::Box& box)
@@ -677,8 +745,11 @@ struct DevArgs {
     const float* e2s;
     const int32_t* mps;
     const int32_t* iroot;
-    // per leaf: the node its traversals start at (k_tile_start)
+    // per leaf: the node its traversals start at, and the sibling subtrees
+    // along the way that come within eps (k_tile_start)
     int32_t* tstart;
+    int2* tsib;
+    int8_t* tnsib;
     // multi-minPts runs: neighbour counts capped at min_pts (null otherwise)
     int32_t* ncount;
 };
@@ -727,6 +798,8 @@ __global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, c
         const TileParams tp = tile_params(a, (int)L);
         int cur = leaf0 + (int)L;
         int start = cur;
+        int ns = 0;  // siblings recorded (-1: more than SIBCAP)
+        int2* sib_out = a.tsib + L * SIBCAP;
         const typename T::Box tb = a.nodebox[cur];
         // the depth of a tree over 64-bit keys with index tie-breaks is
         // below STACK; a longer walk means a corrupt tree: start at the root
@@ -735,16 +808,36 @@ __global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, c
             const int p = parent[cur];
             if (p < 0 || ++steps > STACK) {
                 start = tp.start;
+                ns = -1;
                 break;
             }
             const int4 nm = nmeta[p];
             const int sib = nm.x == cur ? nm.y : nm.x;
             const typename T::Box sb = a.nodebox[sib];
-            if (box_box<D>(tb, sb) <= tp.e2) start = p;
+            if (box_box<D>(tb, sb) <= tp.e2) {
+                start = p;
+                if (ns >= 0 && ns < SIBCAP) {
+                    // the sibling and the last leaf under it
+                    sib_out[ns++] = make_int2(sib, sib >= leaf0 ? sib - leaf0 : nmeta[sib].w);
+                } else {
+                    ns = -1;
+                }
+            }
             cur = p;
         }
         a.tstart[L] = start;
+        a.tnsib[L] = (int8_t)ns;
     }
+}
+
+// the traversal of leaf L's points: from its recorded sibling subtrees, or
+// from its start node when it has more than SIBCAP of them
+template <int D, class V>
+__device__ __forceinline__ void walk(const DevArgs<D>& a, int64_t m, V& v, int* stack, int L)
+{
+    const int ns = a.tnsib[L];
+    if (ns >= 0) traverse_roots<D>(a.nodes, a.nodebox, m, v, stack, a.ctrl, a.tsib + (int64_t)L * SIBCAP, ns);
+    else traverse<D>(a.nodes, a.nodebox, m, v, stack, a.ctrl, a.tstart[L]);
 }
 
 __device__ __forceinline__ int next_leaf(uint32_t* ctr)
@@ -804,7 +897,7 @@ __global__ void __maxnreg__(56) k_pre(DevArgs<D> a)
         v.lcap = a.lcap;
         v.qs = s;
         v.nl = 0;
-        if (__any_sync(FULL, v.act)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
+        if (__any_sync(FULL, v.act)) walk(a, m, v, wm->stack, L);
         if (counts) {
             const bool c = v.cnt >= tp.min_pts;
             a.core[q] = c ? 1 : 0;
@@ -1004,7 +1097,7 @@ __global__ void __maxnreg__(56) k_main(DevArgs<D> a)
             v.valid = in && (tp.min_pts <= 2 || v.qcore || (rule.claims && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
             v.pp = NB<D>::pack(v.p);
-            if (__any_sync(FULL, v.valid)) traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
+            if (__any_sync(FULL, v.valid)) walk(a, m, v, wm->stack, L);
         } else if (KIND == 1) {
             MainSolidV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
@@ -1014,14 +1107,14 @@ __global__ void __maxnreg__(56) k_main(DevArgs<D> a)
             v.pp = NB<D>::pack(v.p);
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
+            walk(a, m, v, wm->stack, L);
         } else {
             MainBoxV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
             v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
-            traverse<D>(a.nodes, a.nodebox, m, v, wm->stack, a.ctrl, a.tstart[L]);
+            walk(a, m, v, wm->stack, L);
         }
     }
 }
@@ -1123,6 +1216,8 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.mps = a.mps;
     d.iroot = a.iroot;
     d.tstart = a.tstart;
+    d.tsib = a.tsib;
+    d.tnsib = a.tnsib;
     d.ncount = a.ncount;
     return d;
 }
