@@ -43,8 +43,9 @@
  *   - Work is enqueued on the given stream (0 = the legacy default stream).
  *     The library owns its device workspaces, one per (device, stream),
  *     grown on demand and freed by dbscan_release_workspaces().
- *   - Sizes: 0 <= n < 2^30 points; dim is 2 or 3; eps > 0 and finite;
- *     min_pts >= 1.
+ *   - Sizes: 0 <= n < 2^30 points; 2 <= dim <= 8 (the paper's 2D and 3D
+ *     sets and its higher-dimensional ones, Table 1; batches: 2 or 3);
+ *     eps > 0 and finite; min_pts >= 1.
  */
 #ifndef GBDBSCAN_H
 #define GBDBSCAN_H
@@ -112,7 +113,7 @@ dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, floa
  *               first coordinate is at points + coord_offsets[b], where
  *               coord_offsets[b] = sum_{c<b} (offsets[c+1]-offsets[c])*dims[c].
  *   offsets     host, count+1 int64 row offsets (offsets[0] = 0, non-decreasing).
- *   dims, eps, min_pts   host, per instance.
+ *   dims, eps, min_pts   host, per instance (dims 2 or 3).
  *   labels_out  device, offsets[count] int32; instance b's labels (relative to
  *               the instance: 0 .. n_b-1, or -1) at labels_out + offsets[b].
  *   core_out    device, offsets[count] bytes or NULL.
@@ -207,10 +208,11 @@ dbscan_status dbscan_set_tuning(int block_size, float cell_factor);
 
 /*
  * Automatic algorithm choice (DBSCAN_ALGO_AUTO) for data of dimension dim
- * (2 or 3): DenseBox when the estimated share of points in dense cells is at
+ * (2 to 8): DenseBox when the estimated share of points in dense cells is at
  * least dense_fraction (in [0, 1]) or the estimated mean cell occupancy is at
  * least occupancy (finite, >= 0), else FDbscan. Defaults: 3D 0.005 and 16
- * (FDbscan's 30-bit Morton grid is coarser than eps there), 2D 0.3 and 16.
+ * (FDbscan's 30-bit Morton grid is coarser than eps there; the same above
+ * 3D), 2D 0.3 and 16.
  * Both arguments negative restore the defaults for dim.
  * DBSCAN_ERR_INVALID_ARG otherwise.
  */

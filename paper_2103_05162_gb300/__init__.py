@@ -136,7 +136,7 @@ def _ptr(t):
 
 def dbscan_run(points, eps: float, min_pts: int, mode="dbscan", algo="densebox", labels_out=None,
                core_out=None, want_core: bool = False, stream=None):
-    """Clusters ``points`` (a CUDA float32 tensor of shape (n, 2) or (n, 3)).
+    """Clusters ``points`` (a CUDA float32 tensor of shape (n, d), 2 <= d <= 8).
 
     Returns ``labels`` (int32, -1 = noise, else the smallest input index of a
     core point of the cluster) or ``(labels, core)`` when ``want_core`` or

@@ -418,7 +418,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     k_inst_roots<<<grid_n(2 * n), 256, 0, s>>>(p.range, p.linst, p.ctrl, p.iroot);
     note_launches(1);
     // union-find init (per point instance parameters)
-    if ((e = cudaMemsetAsync(p.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORDS - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
+    if ((e = cudaMemsetAsync(p.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORK_END - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
         cudaSuccess)
         return e;
     k_binit<<<grid_n(n), 256, 0, s>>>(keys, lb, p.inst, p.db.pdense, p.db.dstart, n, p.labels, p.core);

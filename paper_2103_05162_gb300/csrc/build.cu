@@ -10,9 +10,9 @@ namespace gbd {
 // Each thread strides over the flat coordinate array with a stride that is a
 // multiple of D, so it always sees the same axis.
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(BOUNDS_THREADS) k_bounds(const float* __restrict__ pts, int64_t n,
-                                                           uint32_t* __restrict__ ctrl)
+template <int D, int BT = bounds_threads<D>()>
+__global__ void __launch_bounds__(BT) k_bounds(const float* __restrict__ pts, int64_t n,
+                                               uint32_t* __restrict__ ctrl)
 {
     __shared__ uint32_t s_lo[D], s_hi[D];
     __shared__ int s_bad;
@@ -20,11 +20,11 @@ __global__ void __launch_bounds__(BOUNDS_THREADS) k_bounds(const float* __restri
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     const int64_t total = n * D;
-    const int64_t stride = (int64_t)gridDim.x * BOUNDS_THREADS;
+    const int64_t stride = (int64_t)gridDim.x * BT;
     const int axis = threadIdx.x % D;
     float lo = INFINITY, hi = -INFINITY;
     bool bad = false;
-    for (int64_t i = blockIdx.x * (int64_t)BOUNDS_THREADS + threadIdx.x; i < total; i += stride) {
+    for (int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x; i < total; i += stride) {
         float v = __ldcs(pts + i);
         bad |= !isfinite(v);
         lo = fminf(lo, v);
@@ -68,6 +68,31 @@ __global__ void k_morton32(const float* __restrict__ pts, int64_t n, const uint3
             c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(pts[i * D + k], lo[k]), scale[k])), cmax);
         }
         keys[i] = (uint32_t)interleave<D>(c);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// The same with 64-bit keys (FDBSCAN ordering above 3D).
+template <int D>
+__global__ void k_morton64(const float* __restrict__ pts, int64_t n, const uint32_t* __restrict__ ctrl, int bits,
+                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    float lo[D], scale[D];
+    const float cells = (float)(1u << bits);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        lo[k] = ord2f(ctrl[CTRL_LO + k]);
+        const float ext = __fsub_rn(ord2f(ctrl[CTRL_HI + k]), lo[k]);
+        scale[k] = ext > 0.0f ? __fdiv_rn(cells, ext) : 0.0f;
+    }
+    const uint32_t cmax = (1u << bits) - 1u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            c[k] = cell_index(floorf(__fmul_rn(__fsub_rn(pts[i * D + k], lo[k]), scale[k])), cmax);
+        }
+        keys[i] = interleave<D>(c);
         vals[i] = (uint32_t)i;
     }
 }
@@ -466,12 +491,12 @@ __global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__
             if (atomic_add_acq_rel(&visit[p], 1) == 0) break;
             const int4 mt = nmeta[p];
             Box L, R;
-            L.lo = __ldcg(&nodebox[mt.x].lo); L.hi = __ldcg(&nodebox[mt.x].hi);
-            R.lo = __ldcg(&nodebox[mt.y].lo); R.hi = __ldcg(&nodebox[mt.y].hi);
+            L.lo = ld_cg(&nodebox[mt.x].lo); L.hi = ld_cg(&nodebox[mt.x].hi);
+            R.lo = ld_cg(&nodebox[mt.y].lo); R.hi = ld_cg(&nodebox[mt.y].hi);
             Box U = L;
             T::merge(U, R);
-            __stcg(&nodebox[p].lo, U.lo);
-            __stcg(&nodebox[p].hi, U.hi);
+            st_cg(&nodebox[p].lo, U.lo);
+            st_cg(&nodebox[p].hi, U.hi);
             nodes[p] = T::make_node(L, R, mt.x, mt.y, mt.z, mt.w);
             idx = p;
             p = parent[p];
@@ -493,13 +518,13 @@ cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, con
     const int64_t stride = n > (int64_t(1) << 22) ? n >> 22 : 1;
     int64_t gb = (n / stride + 255) / 256;
     if (gb > 152 * 4) gb = 152 * 4;
-    if (dim == 3) {
-        k_est_insert<3><<<1, 1024, 0, s>>>(points, n, smp, g, eb.table, eb.slot);
-        k_est_count<3><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, eb.table, eb.counts);
-    } else {
-        k_est_insert<2><<<1, 1024, 0, s>>>(points, n, smp, g, eb.table, eb.slot);
-        k_est_count<2><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, eb.table, eb.counts);
-    }
+#define EST_LAUNCH(D)                                                                      \
+    do {                                                                                   \
+        k_est_insert<D><<<1, 1024, 0, s>>>(points, n, smp, g, eb.table, eb.slot);         \
+        k_est_count<D><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, eb.table, eb.counts); \
+    } while (0)
+    GBD_DIM_SWITCH(dim, EST_LAUNCH)
+#undef EST_LAUNCH
     k_est_result<<<1, 1024, 0, s>>>(eb.slot, smp, eb.counts, n, stride, min_pts, eb.result);
     note_launches(3);
     return cudaGetLastError();
@@ -515,9 +540,10 @@ static inline unsigned grid_for(int64_t work, int threads, int max_blocks)
 
 void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStream_t s)
 {
-    const unsigned g = grid_for(n * dim, BOUNDS_THREADS, 152 * 8);
-    if (dim == 3) k_bounds<3><<<g, BOUNDS_THREADS, 0, s>>>(pts, n, ctrl);
-    else k_bounds<2><<<g, BOUNDS_THREADS, 0, s>>>(pts, n, ctrl);
+#define BOUNDS_LAUNCH(D)                                                                            \
+    k_bounds<D><<<grid_for(n * D, bounds_threads<D>(), 152 * 8), bounds_threads<D>(), 0, s>>>(pts, n, ctrl)
+    GBD_DIM_SWITCH(dim, BOUNDS_LAUNCH)
+#undef BOUNDS_LAUNCH
     note_launches(1);
 }
 
@@ -530,12 +556,23 @@ void launch_morton32(const float* pts, int64_t n, int dim, const uint32_t* ctrl,
     note_launches(1);
 }
 
+void launch_morton64(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint64_t* keys,
+                     uint32_t* vals, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+#define M64_LAUNCH(D) k_morton64<D><<<g, 256, 0, s>>>(pts, n, ctrl, bits, keys, vals)
+    GBD_DIM_SWITCH(dim, M64_LAUNCH)
+#undef M64_LAUNCH
+    note_launches(1);
+}
+
 void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* keys, uint32_t* vals,
                     cudaStream_t s)
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
-    if (dim == 3) k_cellkey<3><<<g, 256, 0, s>>>(pts, n, gp, keys, vals);
-    else k_cellkey<2><<<g, 256, 0, s>>>(pts, n, gp, keys, vals);
+#define CK_LAUNCH(D) k_cellkey<D><<<g, 256, 0, s>>>(pts, n, gp, keys, vals)
+    GBD_DIM_SWITCH(dim, CK_LAUNCH)
+#undef CK_LAUNCH
     note_launches(1);
 }
 
@@ -550,8 +587,9 @@ void launch_morton_generic(const float* pts, int64_t n, int dim, const GridParam
 void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, cudaStream_t s)
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
-    if (dim == 3) k_gather<3><<<g, 256, 0, s>>>(pts, perm, n, static_cast<float4*>(sp));
-    else k_gather<2><<<g, 256, 0, s>>>(pts, perm, n, static_cast<float2*>(sp));
+#define GATHER_LAUNCH(D) k_gather<D><<<g, 256, 0, s>>>(pts, perm, n, static_cast<typename Traits<D>::Point*>(sp))
+    GBD_DIM_SWITCH(dim, GATHER_LAUNCH)
+#undef GATHER_LAUNCH
     note_launches(1);
 }
 
@@ -563,12 +601,11 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
     cudaError_t e;
     if ((e = cudaMemsetAsync(t.pdense, 0, (size_t)n, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ctrl + CTRL_NCELLS, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    if (dim == 3)
-        k_dense_classify<3><<<g, 256, 0, s>>>(keys, static_cast<const float4*>(sp), n, min_pts, e2, t.pdense,
-                                              t.dstart, ctrl);
-    else
-        k_dense_classify<2><<<g, 256, 0, s>>>(keys, static_cast<const float2*>(sp), n, min_pts, e2, t.pdense,
-                                              t.dstart, ctrl);
+#define DC_LAUNCH(D)                                                                                         \
+    k_dense_classify<D><<<g, 256, 0, s>>>(keys, static_cast<const typename Traits<D>::Point*>(sp), n, min_pts, e2, \
+                                          t.pdense, t.dstart, ctrl)
+    GBD_DIM_SWITCH(dim, DC_LAUNCH)
+#undef DC_LAUNCH
     k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, 64, t.lf);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
@@ -606,22 +643,37 @@ cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBox
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBoxTemps& t, int2* leafr,
+                                 uint64_t* lkey, uint32_t* ctrl, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+    cudaError_t e;
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, nullptr, nullptr, n, TILE, 64, t.lf);
+    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys, ctrl, 64, leafr, lkey, nullptr);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
                  int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
                  int2* range_out)
 {
     const unsigned gw = grid_for(m_cap * 32, 256, 152 * 16);
     const unsigned g = grid_for(m_cap, 256, 152 * 16);
-    if (dim == 3) k_leaf_boxes<3><<<gw, 256, 0, s>>>(static_cast<const float4*>(sp), leafr, ctrl,
-                                                     static_cast<Traits<3>::Box*>(nodebox));
-    else k_leaf_boxes<2><<<gw, 256, 0, s>>>(static_cast<const float2*>(sp), leafr, ctrl,
-                                             static_cast<Traits<2>::Box*>(nodebox));
+#define LB_LAUNCH(D)                                                                                         \
+    k_leaf_boxes<D><<<gw, 256, 0, s>>>(static_cast<const typename Traits<D>::Point*>(sp), leafr, ctrl,         \
+                                       static_cast<typename Traits<D>::Box*>(nodebox))
+    GBD_DIM_SWITCH(dim, LB_LAUNCH)
+#undef LB_LAUNCH
     k_karras<<<g, 256, 0, s>>>(lkey, ctrl, -1, nmeta, parent, nullptr, range_out);
     cudaMemsetAsync(visit, 0, sizeof(int32_t) * (size_t)(m_cap > 1 ? m_cap - 1 : 1), s);
-    if (dim == 3) k_refit<3><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<Traits<3>::Box*>(nodebox),
-                                               static_cast<Traits<3>::Node*>(nodes), visit);
-    else k_refit<2><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<Traits<2>::Box*>(nodebox),
-                                       static_cast<Traits<2>::Node*>(nodes), visit);
+#define RF_LAUNCH(D)                                                                                         \
+    k_refit<D><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<typename Traits<D>::Box*>(nodebox),          \
+                                 static_cast<typename Traits<D>::Node*>(nodes), visit)
+    GBD_DIM_SWITCH(dim, RF_LAUNCH)
+#undef RF_LAUNCH
     note_launches(3);
 }
 

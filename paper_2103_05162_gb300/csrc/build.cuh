@@ -5,12 +5,38 @@
 
 namespace gbd {
 
-constexpr int BOUNDS_THREADS = 384;  // a multiple of 2 and 3
+constexpr int MAX_DIM = 8;  // points of 2 to 8 dimensions
+
+// calls F(D) with the compile-time dimension D equal to dim (2 .. MAX_DIM;
+// arguments are checked before any launch)
+#define GBD_DIM_SWITCH(dim, F)         \
+    switch (dim) {                     \
+    case 2: F(2); break;               \
+    case 3: F(3); break;               \
+    case 4: F(4); break;               \
+    case 5: F(5); break;               \
+    case 6: F(6); break;               \
+    case 7: F(7); break;               \
+    default: F(8); break;              \
+    }
+
+// bounds kernel block size: a multiple of D, so that a thread striding over
+// the flat coordinates always sees the same axis
+template <int D>
+constexpr int bounds_threads()
+{
+    return D == 5 ? 320 : (D == 7 ? 448 : 384);
+}
+
+// Morton-code bits per axis of FDbscan's keys: 32-bit keys in 2D and 3D,
+// 64-bit keys (at most 63 bits) above
+inline int fdbscan_bits(int dim)
+{
+    return dim == 3 ? 10 : (dim == 2 ? 16 : 63 / dim);
+}
 
 // Slots of the per-workspace control block (uint32 words in device memory).
 enum : int {
-    CTRL_LO = 0,         // 3 words: order-preserving min per axis
-    CTRL_HI = 4,         // 3 words: order-preserving max per axis
     CTRL_NONFINITE = 8,  // nonzero if a coordinate is NaN/Inf
     CTRL_ERR = 9,        // device error bits (ERR_*)
     CTRL_M = 10,         // number of BVH leaves
@@ -20,16 +46,19 @@ enum : int {
     CTRL_KIND_COUNT = 16,  // 3 words: leaves per kind (0 tile, 1 solid tile, 2 dense cell leaf)
     CTRL_KIND_FILL = 19,   // 3 words: fill counters of the per-kind leaf lists
     CTRL_KIND_WORK = 22,   // 3 words: work counters of the per-kind main kernels
-    CTRL_WORDS = 32
+    CTRL_WORK_END = 25,    // end of the per-phase counters (cleared before each phase)
+    CTRL_LO = 32,          // MAX_DIM words: order-preserving min per axis
+    CTRL_HI = 40,          // MAX_DIM words: order-preserving max per axis
+    CTRL_WORDS = 48
 };
 
 constexpr unsigned ERR_STACK = 2u;  // traversal/refit limits exceeded (cannot happen for valid trees)
 
 struct GridParams {
-    float lo[3];
-    float scale[3];     // per-axis scale (generic Morton codes)
-    float inv_h;        // 1 / cell side (DenseBox cells)
-    uint32_t cmax[3];   // largest cell index per axis
+    float lo[MAX_DIM];
+    float scale[MAX_DIM];     // per-axis scale (generic Morton codes)
+    float inv_h;              // 1 / cell side (DenseBox cells)
+    uint32_t cmax[MAX_DIM];   // largest cell index per axis
     int bits;           // bits per axis in the key
     int morton;         // 1: interleave, 0: pack axis by axis
 };
@@ -95,11 +124,21 @@ template <int D>
 __device__ __forceinline__ uint64_t interleave(const uint32_t* c)
 {
     if (D == 3) return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
-    return spread2(c[0]) | (spread2(c[1]) << 1);
+    if (D == 2) return spread2(c[0]) | (spread2(c[1]) << 1);
+    // above 3D: bit b of axis k goes to bit b * D + k (63 / D bits per axis)
+    uint64_t key = 0;
+#pragma unroll
+    for (int b = 0; b < 63 / D; ++b)
+#pragma unroll
+        for (int k = 0; k < D; ++k) key |= (uint64_t)((c[k] >> b) & 1u) << (b * D + k);
+    return key;
 }
 
 void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStream_t s);
 void launch_morton32(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint32_t* keys,
+                     uint32_t* vals, cudaStream_t s);
+// FDbscan keys above 3D: 64-bit Morton codes, `bits` per axis
+void launch_morton64(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint64_t* keys,
                      uint32_t* vals, cudaStream_t s);
 void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* keys, uint32_t* vals,
                     cudaStream_t s);
@@ -111,6 +150,8 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
                                    cudaStream_t s);
 cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBoxTemps& t, int2* leafr,
                                uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
+cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBoxTemps& t, int2* leafr,
+                                 uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
                  int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
                  int2* range_out = nullptr);

@@ -44,10 +44,14 @@ dbscan_status cuda_error(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_error(e_, #x);   \
     } while (0)
 
+// (above 3D the 3D thresholds: FDbscan's Morton grid is coarse there too)
 Tuning g_tuning = {128,
                    1.0f,
-                   {0.0f, 0.0f, DEFAULT_AUTO_FRACTION_2D, DEFAULT_AUTO_FRACTION_3D},
-                   {0.0f, 0.0f, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY}};
+                   {0.0f, 0.0f, DEFAULT_AUTO_FRACTION_2D, DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D,
+                    DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D,
+                    DEFAULT_AUTO_FRACTION_3D},
+                   {0.0f, 0.0f, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY,
+                    DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY}};
 
 // ---------------------------------------------------------------------------
 // launch counting and opt-in per-stage timing (CUDA events on the stream)
@@ -158,13 +162,25 @@ int64_t leaf_cap(int64_t n, int algo)
     return n;  // tiles hold 1..TILE points, dense cells any number
 }
 
+// bytes of a sorted point, a box and a node record in `dim` dimensions
+void record_sizes(int dim, size_t* pt, size_t* box, size_t* node)
+{
+#define SIZES(D)                                       \
+    do {                                               \
+        *pt = sizeof(typename Traits<D>::Point);       \
+        *box = sizeof(typename Traits<D>::Box);        \
+        *node = sizeof(typename Traits<D>::Node);      \
+    } while (0)
+    GBD_DIM_SWITCH(dim, SIZES)
+#undef SIZES
+}
+
 size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, bool counts = false)
 {
     Carver c(base);
     const int64_t mc = leaf_cap(n, algo);
-    const size_t pt = dim == 3 ? sizeof(float4) : sizeof(float2);
-    const size_t box = dim == 3 ? sizeof(Traits<3>::Box) : sizeof(Traits<2>::Box);
-    const size_t node = dim == 3 ? sizeof(Traits<3>::Node) : sizeof(Traits<2>::Node);
+    size_t pt = 0, box = 0, node = 0;
+    record_sizes(dim, &pt, &box, &node);
     p.ctrl = c.take<uint32_t>(CTRL_WORDS);
     p.keys = c.take<uint64_t>(n);
     p.keys_alt = c.take<uint64_t>(n);
@@ -317,7 +333,7 @@ dbscan_status check_run_args(const void* points, int64_t n, int dim, float eps, 
                              const void* labels_out)
 {
     if (n < 0 || n >= (int64_t(1) << 30)) return set_error(DBSCAN_ERR_INVALID_ARG, "n = %lld out of range [0, 2^30)", (long long)n);
-    if (dim != 2 && dim != 3) return set_error(DBSCAN_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", dim);
+    if (dim < 2 || dim > MAX_DIM) return set_error(DBSCAN_ERR_INVALID_ARG, "dim must be in [2, 8] (got %d)", dim);
     if (!(eps > 0.0f) || !std::isfinite(eps)) return set_error(DBSCAN_ERR_INVALID_ARG, "eps must be positive and finite");
     if (min_pts < 1) return set_error(DBSCAN_ERR_INVALID_ARG, "min_pts must be >= 1 (got %d)", min_pts);
     if (mode != DBSCAN_MODE_DBSCAN && mode != DBSCAN_MODE_DBSCAN_STAR)
@@ -335,7 +351,7 @@ GridParams densebox_grid(const float* lo, const float* hi, int dim, float eps, f
 {
     GridParams g{};
     double h = (double)factor * (double)eps / std::sqrt((double)dim);
-    const int maxbits = dim == 3 ? 21 : 31;
+    const int maxbits = dim == 3 ? 21 : (dim == 2 ? 31 : 63 / dim);  // 64-bit keys
     const double maxcells = std::ldexp(1.0, maxbits);
     double ext_max = 0.0;
     for (int k = 0; k < dim; ++k) ext_max = std::fmax(ext_max, (double)hi[k] - (double)lo[k]);
@@ -370,8 +386,9 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     w->last_algo = algo;
     w->last_dense_fraction = -1.0f;
     w->last_occupancy = -1.0f;
-    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, 4 * sizeof(uint32_t), s));
-    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, 5 * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, MAX_DIM * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, MAX_DIM * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_NONFINITE, 0, sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_M, 0, 2 * sizeof(uint32_t), s));
     T.begin(ST_BOUNDS);
     launch_bounds(points, n, dim, p.ctrl, s);
@@ -386,7 +403,7 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
                          hc[CTRL_ERR]);
     }
     if (hc[CTRL_NONFINITE] != 0) return set_error(DBSCAN_ERR_NONFINITE, "input coordinates contain NaN or Inf");
-    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    float lo[MAX_DIM] = {}, hi[MAX_DIM] = {};
     for (int k = 0; k < dim; ++k) {
         lo[k] = ord2f(hc[CTRL_LO + k]);
         hi[k] = ord2f(hc[CTRL_HI + k]);
@@ -423,8 +440,26 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     const int64_t m_cap = leaf_cap(n, algo);
     const uint32_t* perm = nullptr;
 
-    if (algo == DBSCAN_ALGO_FDBSCAN) {
-        const int bits = dim == 3 ? 10 : 16;
+    if (algo == DBSCAN_ALGO_FDBSCAN && dim > 3) {
+        // 64-bit Morton codes
+        const int bits = fdbscan_bits(dim);
+        uint64_t* k64 = static_cast<uint64_t*>(p.keys);
+        T.begin(ST_KEYS);
+        launch_morton64(points, n, dim, p.ctrl, bits, k64, p.vals, s);
+        T.end();
+        T.begin(ST_SORT);
+        TRY_CUDA(sort_pairs_u64(k64, p.vals, n, bits * dim, sb, s, &in_alt));
+        T.end();
+        const uint64_t* keys_sorted = in_alt ? static_cast<uint64_t*>(p.keys_alt) : k64;
+        perm = in_alt ? p.vals_alt : p.vals;
+        T.begin(ST_GATHER);
+        launch_gather(points, perm, n, dim, p.sp, s);
+        T.end();
+        T.begin(ST_LEAVES);
+        TRY_CUDA(launch_tile_leaves64(keys_sorted, n, p.db, p.leafr, p.lkey, p.ctrl, s));
+        T.end();
+    } else if (algo == DBSCAN_ALGO_FDBSCAN) {
+        const int bits = fdbscan_bits(dim);
         uint32_t* k32 = static_cast<uint32_t*>(p.keys);
         T.begin(ST_KEYS);
         launch_morton32(points, n, dim, p.ctrl, bits, k32, p.vals, s);
@@ -679,6 +714,9 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
     for (int32_t b = 0; b < count; ++b) {
         const int64_t nb = offsets[b + 1] - offsets[b];
         if (nb < 0) return set_error(DBSCAN_ERR_INVALID_ARG, "offsets must be non-decreasing (instance %d)", b);
+        if (dims[b] != 2 && dims[b] != 3)
+            return set_error(DBSCAN_ERR_INVALID_ARG, "instance %d: batches take 2D or 3D instances (got %d)", b,
+                             dims[b]);
         dbscan_status st = check_run_args(points, nb, dims[b], eps[b], min_pts[b], mode, algo, labels_out);
         if (st != DBSCAN_OK) return set_error(st, "instance %d: %s", b, t_err.c_str());
         coords += nb * dims[b];
@@ -787,7 +825,7 @@ dbscan_status dbscan_last_choice(dbscan_stream stream, int* algo_out, float* est
 dbscan_status dbscan_set_auto_threshold(int dim, float dense_fraction, float occupancy)
 {
     t_err.clear();
-    if (dim != 2 && dim != 3) return set_error(DBSCAN_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", dim);
+    if (dim < 2 || dim > MAX_DIM) return set_error(DBSCAN_ERR_INVALID_ARG, "dim must be in [2, 8] (got %d)", dim);
     if (dense_fraction < 0.0f && occupancy < 0.0f) {  // restore the defaults
         g_tuning.auto_fraction[dim] = dim == 2 ? DEFAULT_AUTO_FRACTION_2D : DEFAULT_AUTO_FRACTION_3D;
         g_tuning.auto_occupancy[dim] = DEFAULT_AUTO_OCCUPANCY;

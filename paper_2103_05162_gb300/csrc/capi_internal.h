@@ -41,8 +41,8 @@ struct Tuning {
     // DBSCAN_ALGO_AUTO, per dimension (index 2, 3): DenseBox from this
     // estimated dense-point share up, or from this estimated mean cell
     // occupancy up
-    float auto_fraction[4];
-    float auto_occupancy[4];
+    float auto_fraction[9];
+    float auto_occupancy[9];
 };
 // defaults from measurements on GB300: in 3D FDbscan's 10-bit Morton grid is
 // coarser than eps and DenseBox wins as soon as a few dense cells exist; in

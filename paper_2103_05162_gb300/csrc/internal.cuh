@@ -44,6 +44,46 @@ __device__ __forceinline__ float dist2(const float2& a, const float2& b)
     return s;
 }
 
+// A point of 4 to 8 dimensions: 8 floats (32 B: two 16-byte loads), the
+// coordinates from D on unused.
+template <int D>
+struct __align__(16) PtN {
+    float c[8];
+};
+
+// L2-coherent (L1-bypassing) copies of points, for the boxes the refit's
+// threads hand to one another
+__device__ __forceinline__ float4 ld_cg(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_cg(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ void st_cg(float4* p, const float4& v) { __stcg(p, v); }
+__device__ __forceinline__ void st_cg(float2* p, const float2& v) { __stcg(p, v); }
+template <int D>
+__device__ __forceinline__ PtN<D> ld_cg(const PtN<D>* p)
+{
+    PtN<D> r;
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = __ldcg(q), b = __ldcg(q + 1);
+    r.c[0] = a.x; r.c[1] = a.y; r.c[2] = a.z; r.c[3] = a.w;
+    r.c[4] = b.x; r.c[5] = b.y; r.c[6] = b.z; r.c[7] = b.w;
+    return r;
+}
+template <int D>
+__device__ __forceinline__ void st_cg(PtN<D>* p, const PtN<D>& v)
+{
+    float4* q = reinterpret_cast<float4*>(p);
+    __stcg(q, make_float4(v.c[0], v.c[1], v.c[2], v.c[3]));
+    __stcg(q + 1, make_float4(v.c[4], v.c[5], v.c[6], v.c[7]));
+}
+
+template <int D>
+__device__ __forceinline__ float dist2(const PtN<D>& a, const PtN<D>& b)
+{
+    float s = sqr_rn(__fsub_rn(a.c[0], b.c[0]));
+#pragma unroll
+    for (int k = 1; k < D; ++k) s = __fadd_rn(s, sqr_rn(__fsub_rn(a.c[k], b.c[k])));
+    return s;
+}
+
 // Gap between a coordinate p and the interval [lo, hi]: max(lo - p, p - hi, 0),
 // each difference rounded. Rounding is monotone, so for every y in [lo, hi]
 // |fl(p - y)| >= gap, and the squared box distance below is a lower bound of
@@ -115,12 +155,106 @@ __device__ __forceinline__ f32x2 gap2_rn2(f32x2 alo, f32x2 ahi, f32x2 blo, f32x2
 
 // ---------------------------------------------------------------------------
 // Per-dimension storage traits.
-//   Point: sorted coordinates (float4 with w unused in 3D, float2 in 2D).
-//   Box:   an axis-aligned box, 3D (lo.xyz in a, hi.xyz in b) / 2D (lo.xy, hi.xy in a).
+//   Point: sorted coordinates (float2 in 2D, float4 with w unused in 3D,
+//          PtN<D> from 4 to 8 dimensions).
+//   Box:   an axis-aligned box (lo, hi points).
 //   Node:  an internal BVH node holding both children's boxes, their indices,
 //          the split (last leaf of the left child) and the last leaf it covers.
+// The general template covers 4 to 8 dimensions; 2 and 3 are specialised.
 // ---------------------------------------------------------------------------
-template <int D> struct Traits;
+template <int D> struct Traits {
+    static_assert(D >= 4 && D <= 8, "dimensions 2 to 8");
+    using Point = PtN<D>;
+    struct Box { Point lo, hi; };
+    // per axis (left lo, right lo, left hi, right hi), then (left child,
+    // right child, split, last leaf): 16 D + 16 bytes
+    struct Node { float4 ax[D]; int4 m; };
+
+    __device__ static __forceinline__ Point load_point(const float* p, int64_t i)
+    {
+        Point r;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r.c[k] = k < D ? p[D * i + k] : 0.0f;
+        return r;
+    }
+    __device__ static __forceinline__ float coord(const Point& p, int k) { return p.c[k]; }
+    __device__ static __forceinline__ Box point_box(const Point& p) { return Box{p, p}; }
+    __device__ static __forceinline__ Box empty_box()
+    {
+        Box b;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            b.lo.c[k] = k < D ? INFINITY : 0.0f;
+            b.hi.c[k] = k < D ? -INFINITY : 0.0f;
+        }
+        return b;
+    }
+    __device__ static __forceinline__ void grow(Box& b, const Point& p)
+    {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            b.lo.c[k] = fminf(b.lo.c[k], p.c[k]);
+            b.hi.c[k] = fmaxf(b.hi.c[k], p.c[k]);
+        }
+    }
+    __device__ static __forceinline__ void merge(Box& b, const Box& o)
+    {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            b.lo.c[k] = fminf(b.lo.c[k], o.lo.c[k]);
+            b.hi.c[k] = fmaxf(b.hi.c[k], o.hi.c[k]);
+        }
+    }
+    __device__ static __forceinline__ Box shfl_xor(const Box& b, int m)
+    {
+        Box r = b;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            r.lo.c[k] = __shfl_xor_sync(FULL, b.lo.c[k], m);
+            r.hi.c[k] = __shfl_xor_sync(FULL, b.hi.c[k], m);
+        }
+        return r;
+    }
+    __device__ static __forceinline__ float box_dist2(const Point& p, const Box& b)
+    {
+        float s = sqr_rn(gap_rn(b.lo.c[0], b.hi.c[0], p.c[0]));
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = __fadd_rn(s, sqr_rn(gap_rn(b.lo.c[k], b.hi.c[k], p.c[k])));
+        return s;
+    }
+    __device__ static __forceinline__ float box_box_dist2(const Box& a, const Box& b)
+    {
+        float s = sqr_rn(gap2_rn(a.lo.c[0], a.hi.c[0], b.lo.c[0], b.hi.c[0]));
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = __fadd_rn(s, sqr_rn(gap2_rn(a.lo.c[k], a.hi.c[k], b.lo.c[k], b.hi.c[k])));
+        return s;
+    }
+    __device__ static __forceinline__ float diag2(const Box& b) { return dist2(b.lo, b.hi); }
+    __device__ static __forceinline__ float far_dist2(const Point& p, const Box& b)
+    {
+        float s = sqr_rn(fmaxf(__fsub_rn(p.c[0], b.lo.c[0]), __fsub_rn(b.hi.c[0], p.c[0])));
+#pragma unroll
+        for (int k = 1; k < D; ++k)
+            s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(p.c[k], b.lo.c[k]), __fsub_rn(b.hi.c[k], p.c[k]))));
+        return s;
+    }
+    __device__ static __forceinline__ float box_far2(const Box& a, const Box& b)
+    {
+        float s = sqr_rn(fmaxf(__fsub_rn(b.hi.c[0], a.lo.c[0]), __fsub_rn(a.hi.c[0], b.lo.c[0])));
+#pragma unroll
+        for (int k = 1; k < D; ++k)
+            s = __fadd_rn(s, sqr_rn(fmaxf(__fsub_rn(b.hi.c[k], a.lo.c[k]), __fsub_rn(a.hi.c[k], b.lo.c[k]))));
+        return s;
+    }
+    __device__ static __forceinline__ Node make_node(const Box& L, const Box& R, int left, int right, int split, int last)
+    {
+        Node n;
+#pragma unroll
+        for (int k = 0; k < D; ++k) n.ax[k] = make_float4(L.lo.c[k], R.lo.c[k], L.hi.c[k], R.hi.c[k]);
+        n.m = make_int4(left, right, split, last);
+        return n;
+    }
+};
 
 template <> struct Traits<3> {
     using Point = float4;

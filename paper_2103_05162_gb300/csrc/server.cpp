@@ -46,7 +46,7 @@ struct Job {
     int algo;
     int32_t* labels;
     uint8_t* core;
-    bool mergeable;  // batches take an explicit algorithm: automatic-choice jobs run alone
+    bool mergeable;  // batches take 2D/3D and an explicit algorithm: other jobs run alone
     size_t bytes;
     Clock::time_point t_submit, t_done;
     bool done = false;
@@ -246,7 +246,7 @@ dbscan_status dbscan_server_submit(dbscan_server* srv, const float* points, int6
     j->algo = algo;
     j->labels = labels_out;
     j->core = core_out;
-    j->mergeable = algo != DBSCAN_ALGO_AUTO;
+    j->mergeable = algo != DBSCAN_ALGO_AUTO && dim <= 3;
     j->bytes = bytes;
     j->t_submit = Clock::now();
     {

@@ -38,8 +38,75 @@ namespace {
 constexpr int STACK = 128;  // > the largest possible tree depth (97 for 64-bit keys + index tie-break)
 
 // Node access and the box tests of both children at once (packed pairs: the
-// left child in the low half, the right child in the high half).
-template <int D> struct NB;
+// left child in the low half, the right child in the high half). The general
+// template covers 4 to 8 dimensions; 2 and 3 are specialised.
+template <int D> struct NB {
+    using T = Traits<D>;
+    struct PP { f32x2 c[D]; };
+    __device__ static __forceinline__ PP pack(const typename T::Point& p)
+    {
+        PP r;
+#pragma unroll
+        for (int k = 0; k < D; ++k) r.c[k] = pk2(p.c[k], p.c[k]);
+        return r;
+    }
+    __device__ static __forceinline__ typename T::Node load(const typename T::Node* n, int i)
+    {
+        typename T::Node r;
+#pragma unroll
+        for (int k = 0; k < D; ++k) r.ax[k] = __ldg(&n[i].ax[k]);
+        r.m = __ldg(&n[i].m);
+        return r;
+    }
+    __device__ static __forceinline__ typename T::Box box_l(const typename T::Node& n)
+    {
+        typename T::Box b = T::empty_box();
+#pragma unroll
+        for (int k = 0; k < D; ++k) { b.lo.c[k] = n.ax[k].x; b.hi.c[k] = n.ax[k].z; }
+        return b;
+    }
+    __device__ static __forceinline__ typename T::Box box_r(const typename T::Node& n)
+    {
+        typename T::Box b = T::empty_box();
+#pragma unroll
+        for (int k = 0; k < D; ++k) { b.lo.c[k] = n.ax[k].y; b.hi.c[k] = n.ax[k].w; }
+        return b;
+    }
+    __device__ static __forceinline__ void pd2(const typename T::Node& n, const PP& p, float& dl, float& dr)
+    {
+        f32x2 s = sqr2(gap_rn2(pk2(n.ax[0].x, n.ax[0].y), pk2(n.ax[0].z, n.ax[0].w), p.c[0]));
+#pragma unroll
+        for (int k = 1; k < D; ++k)
+            s = add2(s, sqr2(gap_rn2(pk2(n.ax[k].x, n.ax[k].y), pk2(n.ax[k].z, n.ax[k].w), p.c[k])));
+        unpk2(s, dl, dr);
+    }
+    __device__ static __forceinline__ void bd2(const typename T::Node& n, const typename T::Box& q, float& dl,
+                                               float& dr)
+    {
+        f32x2 s = sqr2(gap2_rn2(pk2(q.lo.c[0], q.lo.c[0]), pk2(q.hi.c[0], q.hi.c[0]), pk2(n.ax[0].x, n.ax[0].y),
+                                pk2(n.ax[0].z, n.ax[0].w)));
+#pragma unroll
+        for (int k = 1; k < D; ++k)
+            s = add2(s, sqr2(gap2_rn2(pk2(q.lo.c[k], q.lo.c[k]), pk2(q.hi.c[k], q.hi.c[k]),
+                                      pk2(n.ax[k].x, n.ax[k].y), pk2(n.ax[k].z, n.ax[k].w))));
+        unpk2(s, dl, dr);
+    }
+    __device__ static __forceinline__ float pbox(const typename T::Point& p, const typename T::Box& b)
+    {
+        return T::box_dist2(p, b);
+    }
+    __device__ static __forceinline__ float bbox(const typename T::Box& q, const typename T::Box& b)
+    {
+        return T::box_box_dist2(q, b);
+    }
+    __device__ static __forceinline__ typename T::Point shfl(const typename T::Point& p, int src)
+    {
+        typename T::Point r = p;
+#pragma unroll
+        for (int k = 0; k < D; ++k) r.c[k] = __shfl_sync(FULL, p.c[k], src);
+        return r;
+    }
+};
 template <> struct NB<3> {
     using T = Traits<3>;
     struct PP { f32x2 x, y, z; };  // a point's coordinates, each twice
@@ -133,7 +200,28 @@ template <> struct NB<2> {
 
 // Up to 32 staged points by coordinate (structure of arrays): two
 // neighbouring points load as one packed pair per axis.
-template <int D> struct SoA;
+template <int D> struct __align__(16) SoA {
+    float c[D][32];
+    __device__ __forceinline__ void put(int l, const typename Traits<D>::Point& p)
+    {
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[k][l] = p.c[k];
+    }
+    __device__ __forceinline__ void d2pair(const typename NB<D>::PP& p, int u, float& d0, float& d1) const
+    {
+        f32x2 s = sqr2(sub2(p.c[0], *reinterpret_cast<const f32x2*>(&c[0][u])));
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = add2(s, sqr2(sub2(p.c[k], *reinterpret_cast<const f32x2*>(&c[k][u]))));
+        unpk2(s, d0, d1);
+    }
+    __device__ __forceinline__ float d2(const typename Traits<D>::Point& p, int u) const
+    {
+        float s = sqr_rn(__fsub_rn(p.c[0], c[0][u]));
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = __fadd_rn(s, sqr_rn(__fsub_rn(p.c[k], c[k][u])));
+        return s;
+    }
+};
 template <> struct __align__(16) SoA<3> {
     float x[32], y[32], z[32];
     __device__ __forceinline__ void put(int l, const float4& p) { x[l] = p.x; y[l] = p.y; z[l] = p.z; }
@@ -755,7 +843,10 @@ struct DevArgs {
 };
 
 template <int D>
-__device__ __forceinline__ float box_box(const typename Traits<D>::Box& a, const typename Traits<D>::Box& b);
+__device__ __forceinline__ float box_box(const typename Traits<D>::Box& a, const typename Traits<D>::Box& b)
+{
+    return Traits<D>::box_box_dist2(a, b);
+}
 template <>
 __device__ __forceinline__ float box_box<3>(const Traits<3>::Box& a, const Traits<3>::Box& b)
 {
@@ -847,9 +938,17 @@ __device__ __forceinline__ int next_leaf(uint32_t* ctr)
     return __shfl_sync(FULL, L, 0);
 }
 
-// (56 registers: nine 128-thread blocks per SM)
+// Register caps of the traversal kernels: 56 in 2D and 3D (nine 128-thread
+// blocks per SM, measured fastest on the 16M halo workload); more above 3D,
+// where a point and its packed copy take 3 D registers
 template <int D>
-__global__ void __maxnreg__(56) k_pre(DevArgs<D> a)
+constexpr int traversal_regs()
+{
+    return D <= 3 ? 56 : (D <= 5 ? 96 : 128);
+}
+
+template <int D>
+__global__ void __maxnreg__(traversal_regs<D>()) k_pre(DevArgs<D> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
@@ -1062,10 +1161,8 @@ __global__ void k_kinds_write(const int2* __restrict__ leafr, const uint8_t* __r
 
 // The main phase for the leaves of one kind (KIND 0: MainPtV, 1: MainSolidV,
 // 2: MainBoxV), taken from the kind's list through a work counter.
-// (56 registers: nine 128-thread blocks per SM; measured faster than the
-// unconstrained 60-64 on the 16M halo workload)
 template <int D, int KIND>
-__global__ void __maxnreg__(56) k_main(DevArgs<D> a)
+__global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
@@ -1262,7 +1359,7 @@ void run_main(const ClusterArgs& a, cudaStream_t s)
 cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORDS - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
+    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORK_END - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
         cudaSuccess)
         return e;
     int64_t gn = (a.n + 255) / 256;
@@ -1276,7 +1373,7 @@ cudaError_t launch_cluster_init(const ClusterArgs& a, cudaStream_t s)
 cudaError_t launch_cluster_from_counts(const ClusterArgs& a, int min_pts, cudaStream_t s)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORDS - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
+    if ((e = cudaMemsetAsync(a.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORK_END - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
         cudaSuccess)
         return e;
     int64_t gn = (a.n + 255) / 256;
@@ -1295,8 +1392,9 @@ cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
 {
     int64_t gm = (a.m_cap + 255) / 256;
     if (gm > 152 * 8) gm = 152 * 8;
-    if (a.dim == 3) k_tile_start<3><<<(unsigned)gm, 256, 0, s>>>(dev_args<3>(a), a.parent, a.nmeta);
-    else k_tile_start<2><<<(unsigned)gm, 256, 0, s>>>(dev_args<2>(a), a.parent, a.nmeta);
+#define TS_LAUNCH(D) k_tile_start<D><<<(unsigned)gm, 256, 0, s>>>(dev_args<D>(a), a.parent, a.nmeta)
+    GBD_DIM_SWITCH(a.dim, TS_LAUNCH)
+#undef TS_LAUNCH
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1309,7 +1407,9 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
     cudaError_t e;
     // points that keep no list (instances of a batch with minPts <= 2) read 0
     if (a.lcap > 0 && (e = cudaMemsetAsync(a.nbr, 0, (size_t)a.n, s)) != cudaSuccess) return e;
-    if (a.dim == 3) run_pre<3>(a, s); else run_pre<2>(a, s);
+#define PRE_RUN(D) run_pre<D>(a, s)
+    GBD_DIM_SWITCH(a.dim, PRE_RUN)
+#undef PRE_RUN
     note_launches(1);
     if (a.lcap > 0 && !a.ncount) {  // (several minPts: claims per minPts)
         int64_t gn = (a.n + 255) / 256;
@@ -1322,7 +1422,9 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
 
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
 {
-    if (a.dim == 3) run_main<3>(a, s); else run_main<2>(a, s);
+#define MAIN_RUN(D) run_main<D>(a, s)
+    GBD_DIM_SWITCH(a.dim, MAIN_RUN)
+#undef MAIN_RUN
     note_launches(6);
     return cudaGetLastError();
 }

@@ -59,7 +59,8 @@ def _run(lib, pts, n, dim, eps, mp, mode=0, algo=1, labels=1):
 
 def test_argument_errors_are_reported_without_device_work(lib):
     P = 0x1000  # never dereferenced: every call below fails its argument check
-    assert _run(lib, P, 10, 4, 0.1, 2) == 1
+    assert _run(lib, P, 10, 9, 0.1, 2) == 1
+    assert _run(lib, P, 10, 1, 0.1, 2) == 1
     assert b"dim" in lib.dbscan_last_error()
     assert _run(lib, P, 10, 3, 0.0, 2) == 1
     assert _run(lib, P, 10, 3, float("inf"), 2) == 1
@@ -91,13 +92,14 @@ def test_auto_choice_arguments(lib):
     assert lib.dbscan_set_auto_threshold(3, float("nan"), 16.0) == 1
     assert lib.dbscan_set_auto_threshold(3, 0.3, -1.0) == 1
     assert lib.dbscan_set_auto_threshold(3, 0.3, float("inf")) == 1
-    assert lib.dbscan_set_auto_threshold(4, 0.3, 16.0) == 1
+    assert lib.dbscan_set_auto_threshold(9, 0.3, 16.0) == 1
+    assert lib.dbscan_set_auto_threshold(5, 0.3, 16.0) == 0
     assert lib.dbscan_set_auto_threshold(2, 0.3, 16.0) == 0
     assert lib.dbscan_set_auto_threshold(3, -1.0, -1.0) == 0  # defaults
     assert lib.dbscan_last_choice(None, None, None) == 1
     # the automatic choice is accepted by single runs, refused by batches
     P = 0x1000
-    assert _run(lib, P, 10, 4, 0.1, 2, algo=2) == 1 and b"dim" in lib.dbscan_last_error()
+    assert _run(lib, P, 10, 9, 0.1, 2, algo=2) == 1 and b"dim" in lib.dbscan_last_error()
     off = np.array([0, 5], dtype=np.int64)
     dims = np.array([3], dtype=np.int32)
     eps = np.array([0.1], dtype=np.float32)
@@ -128,7 +130,7 @@ def test_multi_argument_errors(lib):
     st = lib.dbscan_run_multi(P, 10, 3, 0.1, mp.ctypes.data, 3, 0, 1, P, None, None)
     assert st == 1 and b"min_pts[1]" in lib.dbscan_last_error()
     mp = np.array([2, 5], dtype=np.int32)
-    assert lib.dbscan_run_multi(P, 10, 4, 0.1, mp.ctypes.data, 2, 0, 1, P, None, None) == 1
+    assert lib.dbscan_run_multi(P, 10, 9, 0.1, mp.ctypes.data, 2, 0, 1, P, None, None) == 1
     assert lib.dbscan_run_multi(P, 10, 3, 0.1, None, 2, 0, 1, P, None, None) == 1
     assert lib.dbscan_run_multi(P, 10, 3, 0.1, mp.ctypes.data, -1, 0, 1, P, None, None) == 1
     assert lib.dbscan_run_multi(P, 10, 3, 0.1, mp.ctypes.data, 5000, 0, 1, P, None, None) == 1

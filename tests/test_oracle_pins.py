@@ -107,6 +107,36 @@ def test_oracle_matches_brute_force_lattice(seed):
         check_against_brute(X, 1.0, mp, mode)
 
 
+HD_CASES = []
+for seed in range(40):
+    rs = np.random.default_rng(3000 + seed)
+    d = int(rs.integers(4, 9))
+    n = int(rs.integers(1, 400))
+    mp = int(rs.choice([1, 2, 3, 5, 10]))
+    mode = int(rs.integers(0, 2))
+    # blobs of sigma 0.03 per axis: typical pair distances grow like sqrt(d)
+    eps = float(np.float32(rs.uniform(0.02, 0.1) * np.sqrt(d)))
+    HD_CASES.append((seed, d, n, mp, mode, eps))
+
+
+@pytest.mark.parametrize("seed,d,n,mp,mode,eps", HD_CASES)
+def test_oracle_matches_brute_force_4_to_8_dims(seed, d, n, mp, mode, eps):
+    """Points of 4 to 8 dimensions (the paper's higher-dimensional sets,
+    Table 1): the 3^d cells of the oracle's grid against all pairs."""
+    X = blobs(n, d, seed, n_blobs=4, sigma=0.03)
+    check_against_brute(X, eps, mp, mode)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_oracle_matches_brute_force_lattice_5_and_7_dims(seed):
+    rs = np.random.default_rng(6000 + seed)
+    d = 5 if seed % 2 else 7
+    n = int(rs.integers(2, 300))
+    X = rs.integers(0, 3, size=(n, d)).astype(np.float32)
+    for mode in (0, 1):
+        check_against_brute(X, 1.0, int(rs.choice([1, 2, 3, 5])), mode)
+
+
 @pytest.mark.parametrize("seed", range(20))
 def test_oracle_matches_brute_force_offset_coordinates(seed):
     """Coordinates near 1e3 with a small eps: differences are rounded."""
