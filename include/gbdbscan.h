@@ -141,6 +141,25 @@ dbscan_status dbscan_run_multi(const float* points, int64_t n, int dim, float ep
                                dbscan_stream stream);
 
 /*
+ * Point sets larger than device memory (out-of-core, one GPU; the paper names
+ * this as future work, Sec. 6): points and outputs in HOST memory. The set is
+ * cut along its widest axis into slabs of at most slab_points points (0: 2^26;
+ * a slab is whole bins of 1/65536 of the extent, so one dense bin may exceed
+ * it); each slab is clustered on the device with the points within eps of it,
+ * twice (exact core flags, then clusters with every point's flag from its own
+ * slab), and clusters that meet across slabs are merged on the host.
+ * Results as dbscan_run_host (core flags and core labels identical, border
+ * labels valid), for n < 2^31; device memory holds one slab at a time.
+ *   core_host   host, n bytes (required: the merge uses the core flags).
+ * DBSCAN_ERR_INVALID_ARG as dbscan_run, or when a slab with its halo would
+ * hold 2^30 points or more; DBSCAN_ERR_NONFINITE for NaN/Inf coordinates.
+ * Synchronous: returns when the outputs are written.
+ */
+dbscan_status dbscan_run_slabs(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,
+                               int algo, int32_t* labels_host, uint8_t* core_host, int64_t slab_points,
+                               dbscan_stream stream);
+
+/*
  * Serving: a request loop that admits clustering jobs as they arrive, by a
  * device-memory budget and a slot limit, and runs admitted jobs concurrently
  * on their own streams. Jobs keep their device state until collected.

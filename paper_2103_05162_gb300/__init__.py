@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = [
     "DbscanError", "MODE_DBSCAN", "MODE_DBSCAN_STAR", "ALGO_FDBSCAN", "ALGO_DENSEBOX", "ALGO_AUTO",
-    "load", "library_path", "dbscan_run", "dbscan_run_host", "dbscan_run_batch", "dbscan_run_multi", "Server",
+    "load", "library_path", "dbscan_run", "dbscan_run_host", "dbscan_run_batch", "dbscan_run_multi", "dbscan_run_slabs", "Server",
     "sort_pairs_u64", "sort_pairs_u64_noalloc", "morton_codes", "lbvh_topology", "set_tuning",
     "set_auto_threshold", "last_choice", "stream_status", "release_workspaces", "profile_enable",
     "profile_collect", "kernel_launches", "last_stats",
@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True):
             "dbscan_run_host": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_batch": [vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp],
             "dbscan_run_multi": [vp, i64, i32, f32, vp, i32, i32, i32, vp, vp, vp],
+            "dbscan_run_slabs": [vp, i64, i32, f32, i32, i32, i32, vp, vp, i64, vp],
             "dbscan_server_create": [sz, i32, ctypes.POINTER(vp)],
             "dbscan_server_submit": [vp, vp, i64, i32, f32, i32, i32, i32, vp, vp, ctypes.POINTER(u64)],
             "dbscan_server_poll": [vp, u64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
@@ -159,6 +160,23 @@ def dbscan_run(points, eps: float, min_pts: int, mode="dbscan", algo="densebox",
         _check(lib.dbscan_run(_ptr(points), n, d, float(eps), int(min_pts), _mode(mode), _algo(algo),
                               _ptr(labels_out), _ptr(core_out), _stream_handle(stream, points.device)))
     return (labels_out, core_out) if core_out is not None else labels_out
+
+
+def dbscan_run_slabs(points: np.ndarray, eps: float, min_pts: int, mode="dbscan", algo="densebox",
+                     slab_points: int = 0, stream=None):
+    """Clusters host ``points`` (float32 (n, d)) slab by slab, for sets larger
+    than device memory. Returns (labels int32[n], core bool[n])."""
+    lib = load()
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    if pts.ndim != 2:
+        raise TypeError("points must have shape (n, dim)")
+    n, d = pts.shape
+    labels = np.empty(n, dtype=np.int32)
+    core = np.empty(n, dtype=np.uint8)
+    _check(lib.dbscan_run_slabs(ctypes.c_void_p(pts.ctypes.data), n, d, float(eps), int(min_pts), _mode(mode),
+                                _algo(algo), ctypes.c_void_p(labels.ctypes.data), ctypes.c_void_p(core.ctypes.data),
+                                int(slab_points), _stream_handle(stream)))
+    return labels, core.astype(bool)
 
 
 def dbscan_run_multi(points, eps: float, min_pts, mode="dbscan", algo="densebox", labels_out=None,

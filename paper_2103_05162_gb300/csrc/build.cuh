@@ -215,6 +215,9 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s);
 // min_pts = max(3, min_pts) (the core flags are exact, so the minPts <= 2
 // forms, which find core points during the main phase, are not needed)
 cudaError_t launch_cluster_from_counts(const ClusterArgs& a, int min_pts, cudaStream_t s);
+// core flags from the caller (device, input order), after launch_cluster_init;
+// the main phase then runs with min_pts = max(3, min_pts) and no lists
+cudaError_t launch_cluster_core_from_input(const ClusterArgs& a, const uint8_t* core_in, cudaStream_t s);
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
 

@@ -562,6 +562,58 @@ dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim
     return DBSCAN_OK;
 }
 
+// Core flags only, in input order (the first pass of slab-wise clustering):
+// the index, neighbour counts capped at min_pts, and the flags they decide.
+dbscan_status run_core_flags(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int algo,
+                             uint8_t* core_out, int32_t* labels_scratch, cudaStream_t s)
+{
+    const int cap_mp = min_pts < 2 ? 2 : min_pts;
+    TRY_CUDA(ensure_arena(w->main, workspace_bytes_multi(n, dim, algo, cap_mp, DBSCAN_MODE_DBSCAN_STAR), s));
+    Plan p;
+    carve_plan(p, w->main.base, n, dim, algo, 0, true);
+    StageTimer T(w, s);
+    ClusterArgs a;
+    dbscan_status st = build_index(w, p, T, points, n, dim, eps, cap_mp, algo, a, s);
+    if (st != DBSCAN_OK) return st;
+    a.min_pts = cap_mp;
+    a.mode = DBSCAN_MODE_DBSCAN_STAR;  // no lists, no claims: only the counts are wanted
+    a.lcap = 0;
+    a.ncount = p.ncount;
+    TRY_CUDA(cudaMemsetAsync(p.ncount, 0, sizeof(int32_t) * (size_t)n, s));
+    TRY_CUDA(launch_cluster_init(a, s));
+    TRY_CUDA(launch_cluster_starts(a, s));
+    TRY_CUDA(launch_cluster_pre(a, s));
+    TRY_CUDA(launch_cluster_from_counts(a, min_pts, s));
+    TRY_CUDA(launch_cluster_final(a, labels_scratch, core_out, s));
+    return DBSCAN_OK;
+}
+
+// Clustering with the core flags given (device, input order): the second pass
+// of slab-wise clustering, where a slab's border points take their flags from
+// the slab that owns them.
+dbscan_status run_with_core(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                            int algo, const uint8_t* core_in, int32_t* labels_out, cudaStream_t s)
+{
+    TRY_CUDA(ensure_arena(w->main, workspace_bytes(n, dim, algo, 3, DBSCAN_MODE_DBSCAN_STAR), s));
+    Plan p;
+    carve_plan(p, w->main.base, n, dim, algo, 0);
+    StageTimer T(w, s);
+    ClusterArgs a;
+    dbscan_status st = build_index(w, p, T, points, n, dim, eps, min_pts, algo, a, s);
+    if (st != DBSCAN_OK) return st;
+    a.min_pts = min_pts < 3 ? 3 : min_pts;  // the core flags are exact: the minPts >= 3 form
+    a.mode = mode;
+    a.lcap = 0;
+    TRY_CUDA(launch_cluster_init(a, s));
+    TRY_CUDA(launch_cluster_core_from_input(a, core_in, s));
+    // no preprocessing ran: every non-core point may have a core neighbour
+    TRY_CUDA(cudaMemsetAsync(p.nbr, 1, (size_t)n, s));
+    TRY_CUDA(launch_cluster_starts(a, s));
+    TRY_CUDA(launch_cluster_main(a, s));
+    TRY_CUDA(launch_cluster_final(a, labels_out, nullptr, s));
+    return DBSCAN_OK;
+}
+
 // Several minPts over one index (the multi-minPts sweep): the tree is built
 // once (DenseBox cells dense for the largest minPts, which makes them dense
 // for every smaller one), preprocessing counts neighbours once with its early
@@ -670,6 +722,26 @@ dbscan_status dbscan_run_multi(const float* points, int64_t n, int dim, float ep
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
     return run_multi(w, points, n, dim, eps, min_pts, count, mode, algo, labels_out, core_out, s);
+}
+
+dbscan_status dbscan_run_slabs(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,
+                               int algo, int32_t* labels_host, uint8_t* core_host, int64_t slab_points,
+                               dbscan_stream stream)
+{
+    t_err.clear();
+    if (n < 0 || n >= (int64_t(1) << 31))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "n = %lld out of range [0, 2^31)", (long long)n);
+    dbscan_status st = check_run_args(points_host, 0, dim, eps, min_pts, mode, algo, labels_host);
+    if (st != DBSCAN_OK) return st;
+    if (n > 0 && (!points_host || !labels_host || !core_host))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "null pointer (points, labels and core flags are all needed)");
+    if (slab_points < 0) return set_error(DBSCAN_ERR_INVALID_ARG, "slab_points must be >= 0");
+    if (n == 0) return DBSCAN_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    return run_slabs(w, points_host, n, dim, eps, min_pts, mode, algo, labels_host, core_host,
+                     slab_points > 0 ? slab_points : (int64_t(1) << 26), s);
 }
 
 dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,

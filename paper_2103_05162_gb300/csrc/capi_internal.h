@@ -72,6 +72,13 @@ size_t workspace_bytes(int64_t n, int dim, int algo, int min_pts, int mode);
 size_t workspace_bytes_multi(int64_t n, int dim, int algo, int max_min_pts, int mode);
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
                            int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+dbscan_status run_core_flags(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int algo,
+                             uint8_t* core_out, int32_t* labels_scratch, cudaStream_t s);
+dbscan_status run_with_core(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                            int algo, const uint8_t* core_in, int32_t* labels_out, cudaStream_t s);
+// host points and outputs, clustered in slabs of at most slab_points points
+dbscan_status run_slabs(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                        int algo, int32_t* labels, uint8_t* core, int64_t slab_points, cudaStream_t s);
 dbscan_status run_multi(Workspace* w, const float* points, int64_t n, int dim, float eps, const int32_t* min_pts,
                         int count, int mode, int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
 // count instances: rows offsets[b]..offsets[b+1]-1 of the concatenation;

@@ -1234,6 +1234,17 @@ __global__ void k_init_from_counts(const uint8_t* __restrict__ pdense, const int
     }
 }
 
+// Core flags given by the caller in input order (core_in[perm[i]]), for
+// clustering a part of a larger point set whose flags were decided with the
+// rest of it; points of dense cells are core in any case (every one of them
+// has at least minPts neighbours inside its cell).
+__global__ void k_core_from_input(const uint32_t* __restrict__ perm, const uint8_t* __restrict__ core_in,
+                                  const uint8_t* __restrict__ pdense, int64_t n, uint8_t* __restrict__ core)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        core[i] = ((pdense && pdense[i]) || core_in[perm[i]]) ? 1 : 0;
+}
+
 // labels[i] = i, or the first point of its dense cell (pre-united, Sec. 4.2);
 // core = 1 in dense cells (and everywhere when minPts == 1)
 __global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __restrict__ dstart, int64_t n,
@@ -1426,6 +1437,15 @@ cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
     GBD_DIM_SWITCH(a.dim, MAIN_RUN)
 #undef MAIN_RUN
     note_launches(6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_core_from_input(const ClusterArgs& a, const uint8_t* core_in, cudaStream_t s)
+{
+    int64_t gn = (a.n + 255) / 256;
+    if (gn > 152 * 16) gn = 152 * 16;
+    k_core_from_input<<<(unsigned)gn, 256, 0, s>>>(a.perm, core_in, a.pdense, a.n, a.core);
+    note_launches(1);
     return cudaGetLastError();
 }
 

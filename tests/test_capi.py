@@ -139,6 +139,19 @@ def test_multi_argument_errors(lib):
     assert lib.dbscan_run_multi(None, 0, 3, 0.1, mp.ctypes.data, 2, 0, 1, None, None, None) == 0
 
 
+def test_slab_argument_errors(lib):
+    H = np.zeros(30, np.float32)
+    lab = np.zeros(10, np.int32)
+    core = np.zeros(10, np.uint8)
+    run = lambda n, dim, pts, l, c, sp: lib.dbscan_run_slabs(  # noqa: E731
+        pts, n, dim, 0.1, 3, 0, 1, l, c, sp, None)
+    assert run(1 << 31, 3, H.ctypes.data, lab.ctypes.data, core.ctypes.data, 0) == 1
+    assert run(10, 9, H.ctypes.data, lab.ctypes.data, core.ctypes.data, 0) == 1
+    assert run(10, 3, H.ctypes.data, lab.ctypes.data, None, 0) == 1 and b"core" in lib.dbscan_last_error()
+    assert run(10, 3, H.ctypes.data, lab.ctypes.data, core.ctypes.data, -5) == 1
+    assert run(0, 3, None, None, None, 0) == 0
+
+
 def test_server_argument_errors(lib):
     h = ctypes.c_void_p()
     assert lib.dbscan_server_create(0, 4, ctypes.byref(h)) == 1
