@@ -12,6 +12,7 @@ Usage:
   python bench.py --mode batch   # one fused batch of 4096 instances vs one run each
   python bench.py --mode serve   # Poisson-arrival serving vs sequential runs
   python bench.py --mode sweep   # several minPts over one index vs one run each
+  python bench.py --mode slabs   # slab-wise clustering of host points (out-of-core path)
 With N > 1 it is launched by torch.distributed.run; each rank clusters its own
 replica of the workload (replicas only: the method has no exchange step on
 one node), and the value is the points of all ranks over the slowest rank's
@@ -434,6 +435,33 @@ def run_sweep_mode(args) -> None:
                     f"DBSCAN mode"}), flush=True)
 
 
+def run_slabs_mode(args) -> None:
+    """Slab-wise clustering of host points (the out-of-core path): copies of
+    the benchmark workload side by side along x, clustered in slabs of
+    --slab-points points; wall time of the whole call (host partition and
+    merge, copies, both device passes)."""
+    import paper_2103_05162_gb300 as gb
+
+    X1, eps = workload(args.n, args.seed)
+    X = np.concatenate([X1 + np.array([float(c), 0.0, 0.0], np.float32) for c in range(args.slab_copies)])
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    algo = gb.ALGO_DENSEBOX if args.algo == "densebox" else gb.ALGO_FDBSCAN
+    gb.dbscan_run_slabs(X[: len(X1)], eps, args.min_pts, algo=algo, slab_points=args.slab_points)  # warm-up
+    ts = []
+    for _ in range(max(1, args.steps)):
+        t = time.perf_counter()
+        gb.dbscan_run_slabs(X, eps, args.min_pts, algo=algo, slab_points=args.slab_points)
+        ts.append(time.perf_counter() - t)
+    tm = float(np.median(ts))
+    print(json.dumps({
+        "metric": "points clustered/sec, slab-wise from host memory", "value": X.shape[0] / tm, "unit": UNIT,
+        "points": int(X.shape[0]), "slab_points": args.slab_points, "seconds_median": tm, "steps": len(ts),
+        "algo": args.algo, "min_pts": args.min_pts,
+        "workload": f"{args.slab_copies} copies of {workload_desc(args.n, eps, args.min_pts)} side by side along x",
+        "timing": "wall clock of dbscan_run_slabs (host partition, gathers, copies, two device passes, merge)"}),
+        flush=True)
+
+
 def _wait_until(target: float) -> float:
     while True:
         now = time.perf_counter()
@@ -550,11 +578,14 @@ def main():
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep"], default="step",
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep", "slabs"], default="step",
                     help="step: the headline line (default); batch: fused batch vs per-instance runs; "
                          "serve: Poisson-arrival serving vs sequential runs; sweep: several minPts over one "
-                         "index vs one run each (these three: 1 GPU, rank 0 only)")
+                         "index vs one run each; slabs: slab-wise clustering from host memory "
+                         "(these four: 1 GPU, rank 0 only)")
     ap.add_argument("--sweep-min-pts", default="2,5,10,20")
+    ap.add_argument("--slab-copies", type=int, default=4)
+    ap.add_argument("--slab-points", type=int, default=1 << 24)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-algos", default="densebox,fdbscan")
@@ -575,7 +606,8 @@ def main():
         if rank == 0:
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-            {"batch": run_batch_mode, "serve": run_serve_mode, "sweep": run_sweep_mode}[args.mode](args)
+            {"batch": run_batch_mode, "serve": run_serve_mode, "sweep": run_sweep_mode,
+             "slabs": run_slabs_mode}[args.mode](args)
         return
     if world > 1:
         import torch

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <thread>
 #include <vector>
 
 #include "capi_internal.h"
@@ -33,6 +34,34 @@ namespace gbd {
 namespace {
 
 constexpr int SLAB_BINS = 65536;
+
+// f(lo, hi, t) over contiguous chunks of [0, n) on up to 16 host threads
+template <class F>
+void parallel_for(int64_t n, F f)
+{
+    int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (n < (int64_t)nt * 65536) nt = (int)std::max<int64_t>(1, n / 65536);
+    if (nt <= 1) {
+        f((int64_t)0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt, t); });
+    for (auto& x : th) x.join();
+}
+
+int host_threads(int64_t n)
+{
+    int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (n < (int64_t)nt * 65536) nt = (int)std::max<int64_t>(1, n / 65536);
+    return nt;
+}
+
+int32_t find_readonly(const std::vector<int32_t>& parent, int32_t x)
+{
+    while (parent[(size_t)x] != x) x = parent[(size_t)x];
+    return x;
+}
 
 int32_t uf_find_host(std::vector<int32_t>& parent, int32_t x)
 {
@@ -71,14 +100,28 @@ dbscan_status run_slabs(Workspace* w, const float* P, int64_t n, int dim, float 
                         int32_t* labels, uint8_t* core, int64_t slab_points, cudaStream_t s)
 {
     // axis of largest extent (and the non-finite check)
+    const int nt = host_threads(n);
+    std::vector<float> tlo((size_t)nt * dim, std::numeric_limits<float>::infinity());
+    std::vector<float> thi((size_t)nt * dim, -std::numeric_limits<float>::infinity());
+    std::vector<int> tbad((size_t)nt, 0);
+    parallel_for(n, [&](int64_t a, int64_t b, int t) {
+        float* l = &tlo[(size_t)t * dim];
+        float* h = &thi[(size_t)t * dim];
+        for (int64_t i = a; i < b; ++i)
+            for (int k = 0; k < dim; ++k) {
+                const float v = P[i * dim + k];
+                if (!std::isfinite(v)) tbad[(size_t)t] = 1;
+                l[k] = std::min(l[k], v);
+                h[k] = std::max(h[k], v);
+            }
+    });
     std::vector<float> lo((size_t)dim, std::numeric_limits<float>::infinity());
     std::vector<float> hi((size_t)dim, -std::numeric_limits<float>::infinity());
-    for (int64_t i = 0; i < n; ++i) {
+    for (int t = 0; t < nt; ++t) {
+        if (tbad[(size_t)t]) return set_error(DBSCAN_ERR_NONFINITE, "input coordinates contain NaN or Inf");
         for (int k = 0; k < dim; ++k) {
-            const float v = P[i * dim + k];
-            if (!std::isfinite(v)) return set_error(DBSCAN_ERR_NONFINITE, "input coordinates contain NaN or Inf");
-            lo[k] = std::min(lo[k], v);
-            hi[k] = std::max(hi[k], v);
+            lo[k] = std::min(lo[k], tlo[(size_t)t * dim + k]);
+            hi[k] = std::max(hi[k], thi[(size_t)t * dim + k]);
         }
     }
     int ax = 0;
@@ -88,21 +131,37 @@ dbscan_status run_slabs(Workspace* w, const float* P, int64_t n, int dim, float 
     const double wbin = ext > 0.0 ? ext / SLAB_BINS : 1.0;
 
     // counting sort of the point indices by bin (stable)
-    std::vector<int64_t> start((size_t)SLAB_BINS + 1, 0);
+    // per-thread histograms over contiguous chunks; chunk t's points of bin b
+    // go after those of chunks < t, so the order within a bin stays the
+    // input order
     std::vector<uint16_t> bin((size_t)n);
-    for (int64_t i = 0; i < n; ++i) {
-        double t = std::floor(((double)P[i * dim + ax] - (double)lo[ax]) / wbin);
-        const int b = t < 0.0 ? 0 : (t >= SLAB_BINS ? SLAB_BINS - 1 : (int)t);
-        bin[(size_t)i] = (uint16_t)b;
-        ++start[(size_t)b + 1];
+    std::vector<int64_t> th((size_t)nt * SLAB_BINS, 0);
+    parallel_for(n, [&](int64_t a, int64_t b, int t) {
+        int64_t* h = &th[(size_t)t * SLAB_BINS];
+        for (int64_t i = a; i < b; ++i) {
+            const double v = std::floor(((double)P[i * dim + ax] - (double)lo[ax]) / wbin);
+            const int c = v < 0.0 ? 0 : (v >= SLAB_BINS ? SLAB_BINS - 1 : (int)v);
+            bin[(size_t)i] = (uint16_t)c;
+            ++h[c];
+        }
+    });
+    std::vector<int64_t> start((size_t)SLAB_BINS + 1, 0);
+    for (int c = 0; c < SLAB_BINS; ++c) {
+        int64_t sum = start[(size_t)c];
+        for (int t = 0; t < nt; ++t) {
+            const int64_t k = th[(size_t)t * SLAB_BINS + c];
+            th[(size_t)t * SLAB_BINS + c] = sum;  // chunk t's first position in bin c
+            sum += k;
+        }
+        start[(size_t)c + 1] = sum;
     }
-    for (int b = 0; b < SLAB_BINS; ++b) start[(size_t)b + 1] += start[(size_t)b];
     std::vector<int32_t> order((size_t)n);
-    {
-        std::vector<int64_t> fill(start.begin(), start.end() - 1);
-        for (int64_t i = 0; i < n; ++i) order[(size_t)fill[bin[(size_t)i]]++] = (int32_t)i;
-    }
+    parallel_for(n, [&](int64_t a, int64_t b, int t) {
+        int64_t* f = &th[(size_t)t * SLAB_BINS];
+        for (int64_t i = a; i < b; ++i) order[(size_t)f[bin[(size_t)i]]++] = (int32_t)i;
+    });
     std::vector<uint16_t>().swap(bin);
+    std::vector<int64_t>().swap(th);
 
     // slabs of whole bins, at most slab_points owned points (at least one bin)
     const int64_t hbins = (int64_t)std::ceil((double)eps / wbin) + 1;
@@ -146,8 +205,10 @@ dbscan_status run_slabs(Workspace* w, const float* P, int64_t n, int dim, float 
 
     auto gather = [&](const Slab& sl) {
         const int64_t m = sl.rows1 - sl.rows0;
-        for (int64_t j = 0; j < m; ++j)
-            std::memcpy(hpts + j * dim, P + (int64_t)order[(size_t)(sl.rows0 + j)] * dim, sizeof(float) * dim);
+        parallel_for(m, [&](int64_t a, int64_t b, int) {
+            for (int64_t j = a; j < b; ++j)
+                std::memcpy(hpts + j * dim, P + (int64_t)order[(size_t)(sl.rows0 + j)] * dim, sizeof(float) * dim);
+        });
         return cudaMemcpyAsync(dpts, hpts, sizeof(float) * (size_t)m * dim, cudaMemcpyHostToDevice, s);
     };
 
@@ -160,7 +221,9 @@ dbscan_status run_slabs(Workspace* w, const float* P, int64_t n, int dim, float 
         if ((e = cudaMemcpyAsync(hcore, dcore_out, (size_t)m, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_error(e, "cudaMemcpyAsync");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
-        for (int64_t r = sl.own0; r < sl.own1; ++r) core[order[(size_t)r]] = hcore[r - sl.rows0];
+        parallel_for(sl.own1 - sl.own0, [&](int64_t a, int64_t b, int) {
+            for (int64_t r = sl.own0 + a; r < sl.own0 + b; ++r) core[order[(size_t)r]] = hcore[r - sl.rows0];
+        });
     }
 
     // pass 2: clusters of slab + halo with the owners' core flags
@@ -168,7 +231,9 @@ dbscan_status run_slabs(Workspace* w, const float* P, int64_t n, int dim, float 
     for (const Slab& sl : slabs) {
         const int64_t m = sl.rows1 - sl.rows0;
         if ((e = gather(sl)) != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync");
-        for (int64_t j = 0; j < m; ++j) hcore[j] = core[order[(size_t)(sl.rows0 + j)]];
+        parallel_for(m, [&](int64_t a, int64_t b, int) {
+            for (int64_t j = a; j < b; ++j) hcore[j] = core[order[(size_t)(sl.rows0 + j)]];
+        });
         if ((e = cudaMemcpyAsync(dcore_in, hcore, (size_t)m, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return cuda_error(e, "cudaMemcpyAsync");
         dbscan_status st = run_with_core(w, dpts, m, dim, eps, min_pts, mode, algo, dcore_in, dlab, s);
@@ -177,30 +242,40 @@ dbscan_status run_slabs(Workspace* w, const float* P, int64_t n, int dim, float 
             cudaSuccess)
             return cuda_error(e, "cudaMemcpyAsync");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
-        for (int64_t j = 0; j < m; ++j) {
-            const int64_t r = sl.rows0 + j;
-            const int32_t gid = order[(size_t)r];
-            // slab labels are the slab's row of a core point of the cluster
-            const int32_t glab = hlab[j] >= 0 ? order[(size_t)(sl.rows0 + hlab[j])] : -1;
-            if (r >= sl.own0 && r < sl.own1) labels[gid] = glab;
-            else if (core[gid] && glab >= 0) halo.emplace_back(gid, glab);
-        }
+        const int ntm = host_threads(m);
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> thalo((size_t)ntm);
+        parallel_for(m, [&](int64_t a, int64_t b, int t) {
+            for (int64_t j = a; j < b; ++j) {
+                const int64_t r = sl.rows0 + j;
+                const int32_t gid = order[(size_t)r];
+                // slab labels are the slab's row of a core point of the cluster
+                const int32_t glab = hlab[j] >= 0 ? order[(size_t)(sl.rows0 + hlab[j])] : -1;
+                if (r >= sl.own0 && r < sl.own1) labels[gid] = glab;
+                else if (core[gid] && glab >= 0) thalo[(size_t)t].emplace_back(gid, glab);
+            }
+        });
+        for (auto& v : thalo) halo.insert(halo.end(), v.begin(), v.end());
     }
     dbscan_status st = workspace_status(w, s);
     if (st != DBSCAN_OK) return st;
 
     // merge across slabs, then the smallest global index of a core point
     std::vector<int32_t> parent((size_t)n);
-    for (int64_t i = 0; i < n; ++i) parent[(size_t)i] = (int32_t)i;
+    parallel_for(n, [&](int64_t a, int64_t b, int) {
+        for (int64_t i = a; i < b; ++i) parent[(size_t)i] = (int32_t)i;
+    });
     for (const auto& h : halo) uf_union_host(parent, labels[h.first], h.second);
+    // (no more writes to parent: the finds below only read it)
+    std::vector<int32_t> root((size_t)n);
+    parallel_for(n, [&](int64_t a, int64_t b, int) {
+        for (int64_t i = a; i < b; ++i) root[(size_t)i] = labels[i] >= 0 ? find_readonly(parent, labels[i]) : -1;
+    });
     std::vector<int32_t> cmin((size_t)n, std::numeric_limits<int32_t>::max());
-    for (int64_t i = 0; i < n; ++i) {
-        if (!core[i]) continue;
-        const int32_t r = uf_find_host(parent, labels[i]);
-        cmin[(size_t)r] = std::min(cmin[(size_t)r], (int32_t)i);
-    }
     for (int64_t i = 0; i < n; ++i)
-        if (labels[i] >= 0) labels[i] = cmin[(size_t)uf_find_host(parent, labels[i])];
+        if (core[i]) cmin[(size_t)root[(size_t)i]] = std::min(cmin[(size_t)root[(size_t)i]], (int32_t)i);
+    parallel_for(n, [&](int64_t a, int64_t b, int) {
+        for (int64_t i = a; i < b; ++i) labels[i] = root[(size_t)i] >= 0 ? cmin[(size_t)root[(size_t)i]] : -1;
+    });
     return DBSCAN_OK;
 }
 
