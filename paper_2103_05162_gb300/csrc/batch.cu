@@ -289,6 +289,8 @@ struct BatchPlan {
     int32_t* tstart;
     int2* tsib;
     int8_t* tnsib;
+    int32_t* llist;
+    int16_t* lcount;
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
@@ -337,6 +339,8 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo, int
     p.tstart = c.take<int32_t>(n);
     p.tsib = c.take<int2>(n * TRAVERSAL_SIBCAP);
     p.tnsib = c.take<int8_t>(n);
+    p.llist = c.take<int32_t>(n * TRAVERSAL_LEAFCAP);
+    p.lcount = c.take<int16_t>(n);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
@@ -434,6 +438,8 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     a.tstart = p.tstart;
     a.tsib = p.tsib;
     a.tnsib = p.tnsib;
+    a.llist = p.llist;
+    a.lcount = p.lcount;
     a.parent = p.parent;
     a.nmeta = p.nmeta;
     a.pdense = p.db.pdense;

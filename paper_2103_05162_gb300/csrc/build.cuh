@@ -161,7 +161,8 @@ void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* p
                         int2* range_out, cudaStream_t s);
 
 // traverse.cu
-constexpr int TRAVERSAL_SIBCAP = 8;  // sibling subtrees recorded per leaf
+constexpr int TRAVERSAL_SIBCAP = 8;   // sibling subtrees recorded per leaf
+constexpr int TRAVERSAL_LEAFCAP = 48; // leaves within eps listed per leaf
 
 struct ClusterArgs {
     const void* sp;        // sorted points
@@ -202,6 +203,8 @@ struct ClusterArgs {
     int32_t* tstart = nullptr;
     int2* tsib = nullptr;    // m_cap * TRAVERSAL_SIBCAP: (node, last leaf) of the sibling subtrees within eps
     int8_t* tnsib = nullptr; // m_cap: how many (-1: more than TRAVERSAL_SIBCAP, use tstart)
+    int32_t* llist = nullptr;  // m_cap * TRAVERSAL_LEAFCAP: the leaves within eps of each leaf's box
+    int16_t* lcount = nullptr; // m_cap: how many (-1: more than TRAVERSAL_LEAFCAP, walk the tree)
     // multi-minPts runs: neighbour counts capped at min_pts (null otherwise)
     int32_t* ncount = nullptr;
 };

@@ -147,6 +147,8 @@ struct Plan {
     int32_t* tstart;
     int2* tsib;
     int8_t* tnsib;
+    int32_t* llist;
+    int16_t* lcount;
     int32_t* labels;
     uint8_t* core;
     uint8_t* nbr;
@@ -212,6 +214,8 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.tstart = c.take<int32_t>(mc);
     p.tsib = c.take<int2>(mc * TRAVERSAL_SIBCAP);
     p.tnsib = c.take<int8_t>(mc);
+    p.llist = c.take<int32_t>(mc * TRAVERSAL_LEAFCAP);
+    p.lcount = c.take<int16_t>(mc);
     p.labels = c.take<int32_t>(n);
     p.core = c.take<uint8_t>(n);
     p.nbr = c.take<uint8_t>(n);
@@ -510,6 +514,8 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     a.tstart = p.tstart;
     a.tsib = p.tsib;
     a.tnsib = p.tnsib;
+    a.llist = p.llist;
+    a.lcount = p.lcount;
     a.parent = p.parent;
     a.nmeta = p.nmeta;
     a.pdense = algo == DBSCAN_ALGO_DENSEBOX ? p.db.pdense : nullptr;

@@ -367,8 +367,9 @@ __device__ __forceinline__ void traverse_roots(const typename Traits<D>::Node* _
 }
 
 // per leaf: at most SIBCAP sibling subtrees are recorded (more: the start
-// node is used instead)
+// node is used instead), and at most LEAFCAP leaves within eps
 constexpr int SIBCAP = TRAVERSAL_SIBCAP;
+constexpr int LEAFCAP = TRAVERSAL_LEAFCAP;
 
 // ---------------------------------------------------------------------------
 // Preprocessing visitor: count neighbours up to minPts (Sec. 3.2, 4.1, 4.2).
@@ -840,6 +841,9 @@ struct DevArgs {
     int8_t* tnsib;
     // multi-minPts runs: neighbour counts capped at min_pts (null otherwise)
     int32_t* ncount;
+    // per leaf: the leaves within eps of its box (k_leaf_lists; null: none)
+    int32_t* llist;
+    int16_t* lcount;
 };
 
 template <int D>
@@ -923,9 +927,93 @@ __global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, c
 
 // the traversal of leaf L's points: from its recorded sibling subtrees, or
 // from its start node when it has more than SIBCAP of them
+// The leaves whose boxes come within eps of each leaf's box (itself
+// excluded), found once per leaf by one thread walking the subtrees recorded
+// by k_tile_start with the leaf box as the query (box-to-box test, exact by
+// the same monotone-rounding argument). Every neighbour of a point of the
+// leaf lies in one of them, so the traversals of both phases can go through
+// the list instead of the tree. More than LEAFCAP leaves: count -1, and the
+// phases walk the tree for that leaf.
+template <int D>
+__global__ void k_leaf_lists(DevArgs<D> a)
+{
+    using T = Traits<D>;
+    const int64_t m = a.ctrl[CTRL_M];
+    const int leaf0 = (int)(m - 1);
+    int stk[64];
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < m; L += (int64_t)gridDim.x * blockDim.x) {
+        const TileParams tp = tile_params(a, (int)L);
+        typename T::Box q;
+        q.lo = a.nodebox[leaf0 + L].lo;
+        q.hi = a.nodebox[leaf0 + L].hi;
+        int32_t* out = a.llist + L * LEAFCAP;
+        int cnt = 0, sp = 0;
+        const int ns = a.tnsib[L];
+        if (ns >= 0) {
+            for (int j = 0; j < ns; ++j) {
+                const int r = a.tsib[L * SIBCAP + j].x;
+                if (r >= leaf0) {  // a leaf sibling: within eps of the box by construction
+                    if (cnt < LEAFCAP) out[cnt] = r - leaf0;
+                    ++cnt;
+                } else if (sp < 64) {
+                    stk[sp++] = r;
+                } else {
+                    cnt = LEAFCAP + 1;
+                }
+            }
+        } else {
+            cnt = LEAFCAP + 1;  // no recorded roots: the phases walk the tree
+        }
+        int64_t steps = 0;
+        while (sp > 0 && cnt <= LEAFCAP) {
+            if (++steps > m) {
+                atomicOr(&a.ctrl[CTRL_ERR], ERR_STACK);
+                cnt = LEAFCAP + 1;
+                break;
+            }
+            const int node = stk[--sp];
+            const auto nd = NB<D>::load(a.nodes, node);
+            float dl, dr;
+            NB<D>::bd2(nd, q, dl, dr);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if ((c ? dr : dl) > tp.e2) continue;
+                const int child = c ? nd.m.y : nd.m.x;
+                if (child >= leaf0) {
+                    if (child - leaf0 != (int)L) {
+                        if (cnt < LEAFCAP) out[cnt] = child - leaf0;
+                        ++cnt;
+                    }
+                } else if (sp < 64) {
+                    stk[sp++] = child;
+                } else {
+                    cnt = LEAFCAP + 1;
+                }
+            }
+        }
+        a.lcount[L] = cnt <= LEAFCAP ? (int16_t)cnt : (int16_t)-1;
+    }
+}
+
 template <int D, class V>
 __device__ __forceinline__ void walk(const DevArgs<D>& a, int64_t m, V& v, int* stack, int L)
 {
+    const int lc = a.lcount ? a.lcount[L] : -1;
+    if (lc >= 0) {
+        // the leaf list: a lane-wise box test per listed leaf, no tree walk
+        const int leaf0 = (int)(m - 1);
+        const int32_t* lst = a.llist + (int64_t)L * LEAFCAP;
+        for (int j = 0; j < lc; ++j) {
+            const int U = __ldg(&lst[j]);
+            if (U < v.mask_lo) continue;
+            typename Traits<D>::Box b;
+            b.lo = a.nodebox[leaf0 + U].lo;
+            b.hi = a.nodebox[leaf0 + U].hi;
+            const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+            if (mk && v.leaf(U, mk, b)) return;
+        }
+        return;
+    }
     const int ns = a.tnsib[L];
     if (ns >= 0) traverse_roots<D>(a.nodes, a.nodebox, m, v, stack, a.ctrl, a.tsib + (int64_t)L * SIBCAP, ns);
     else traverse<D>(a.nodes, a.nodebox, m, v, stack, a.ctrl, a.tstart[L]);
@@ -1326,6 +1414,8 @@ DevArgs<D> dev_args(const ClusterArgs& a)
     d.tstart = a.tstart;
     d.tsib = a.tsib;
     d.tnsib = a.tnsib;
+    d.llist = a.llist;
+    d.lcount = a.lcount;
     d.ncount = a.ncount;
     return d;
 }
@@ -1406,6 +1496,12 @@ cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
 #define TS_LAUNCH(D) k_tile_start<D><<<(unsigned)gm, 256, 0, s>>>(dev_args<D>(a), a.parent, a.nmeta)
     GBD_DIM_SWITCH(a.dim, TS_LAUNCH)
 #undef TS_LAUNCH
+    if (a.llist) {
+#define LL_LAUNCH(D) k_leaf_lists<D><<<(unsigned)gm, 256, 0, s>>>(dev_args<D>(a))
+        GBD_DIM_SWITCH(a.dim, LL_LAUNCH)
+#undef LL_LAUNCH
+        note_launches(1);
+    }
     note_launches(1);
     return cudaGetLastError();
 }
