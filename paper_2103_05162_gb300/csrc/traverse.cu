@@ -374,6 +374,20 @@ constexpr int LEAFCAP = TRAVERSAL_LEAFCAP;
 // ---------------------------------------------------------------------------
 // Preprocessing visitor: count neighbours up to minPts (Sec. 3.2, 4.1, 4.2).
 // ---------------------------------------------------------------------------
+// The bounding box of the points of the lanes with `on` (empty if none): a
+// query box for all of them at once. For p inside it every per-axis gap to a
+// box is at least the box-to-box gap (monotone rounding, same order of the
+// sum), so a box farther than eps from it is farther from each point.
+template <int D>
+__device__ __forceinline__ typename Traits<D>::Box warp_box(const typename Traits<D>::Point& p, bool on)
+{
+    using T = Traits<D>;
+    typename T::Box b = on ? T::point_box(p) : T::empty_box();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
+    return b;
+}
+
 template <int D>
 struct PreV {
     using T = Traits<D>;
@@ -414,11 +428,19 @@ struct PreV {
     }
     __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return act && NB<D>::pbox(p, b) <= e2; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, act); }
+    // list entries are worth a first test against the box of the active queries
+    static constexpr bool PREFILTER = true;
+    static constexpr bool NEEDS_SOLID = false;
+    __device__ __forceinline__ typename T::Box query_box() const { return warp_box<D>(p, act); }
 
-    __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
+    __device__ __forceinline__ bool leaf(int L, unsigned mask, const typename T::Box& box)
+    {
+        return leaf_rec(L, mask, box, __ldg(&leafr[L]), 0);
+    }
+    // the same with the leaf's record (start, end) already loaded
+    __device__ bool leaf_rec(int L, unsigned mask, const typename T::Box& box, int2 r, int)
     {
         if (L == own) return false;
-        const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
         mask &= __ballot_sync(FULL, act);
         // the whole leaf within eps: count it at once
@@ -568,15 +590,22 @@ struct MainPtV {
         hr = valid && dr <= e2;
     }
     __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return valid && NB<D>::pbox(p, b) <= e2; }
+    static constexpr bool PREFILTER = true;
+    static constexpr bool NEEDS_SOLID = true;
+    __device__ __forceinline__ typename T::Box query_box() const { return warp_box<D>(p, valid); }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
-    __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
+    __device__ __forceinline__ bool leaf(int L, unsigned mask, const typename T::Box& box)
+    {
+        return leaf_rec(L, mask, box, __ldg(&leafr[L]), lsolid[L]);
+    }
+    // the same with the leaf's record and solid flag already loaded
+    __device__ bool leaf_rec(int L, unsigned mask, const typename T::Box& box, int2 r, int solid)
     {
         if (L < mask_lo) return false;
-        const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
         const bool cont = ((mask >> lane) & 1u) && T::far_dist2(p, box) <= e2;
-        if (!lsolid[L]) {
+        if (!solid) {
             const int k = e - s;
             if (__popc(mask) < k) {
                 const bool in = lane < k;
@@ -668,6 +697,9 @@ struct MainSolidV {
         hr = valid && dr <= e2;
     }
     __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return valid && NB<D>::pbox(p, b) <= e2; }
+    // the query box is the leaf box, which every listed leaf passes
+    static constexpr bool PREFILTER = false;
+    __device__ __forceinline__ typename T::Box query_box() const { return qb; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
     __device__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -754,6 +786,9 @@ struct MainBoxV {
         hr = dr <= e2;
     }
     __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return NB<D>::bbox(qb, b) <= e2; }
+    // the query box is the leaf box, which every listed leaf passes
+    static constexpr bool PREFILTER = false;
+    __device__ __forceinline__ typename T::Box query_box() const { return qb; }
     __device__ __forceinline__ unsigned root_mask() const { return FULL; }
 
     __device__ bool leaf(int L, unsigned, const typename T::Box& box)
@@ -1000,17 +1035,57 @@ __device__ __forceinline__ void walk(const DevArgs<D>& a, int64_t m, V& v, int* 
 {
     const int lc = a.lcount ? a.lcount[L] : -1;
     if (lc >= 0) {
-        // the leaf list: a lane-wise box test per listed leaf, no tree walk
+        // the leaf list, no tree walk. Per-point queries: each lane tests
+        // one listed leaf against the box of the warp's queries, then the
+        // leaves that pass are taken in list order with the lane-wise test
+        // of each query
         const int leaf0 = (int)(m - 1);
+        const int lane = threadIdx.x & 31;
         const int32_t* lst = a.llist + (int64_t)L * LEAFCAP;
-        for (int j = 0; j < lc; ++j) {
-            const int U = __ldg(&lst[j]);
-            if (U < v.mask_lo) continue;
-            typename Traits<D>::Box b;
-            b.lo = a.nodebox[leaf0 + U].lo;
-            b.hi = a.nodebox[leaf0 + U].hi;
-            const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
-            if (mk && v.leaf(U, mk, b)) return;
+        if constexpr (!V::PREFILTER) {
+            for (int j = 0; j < lc; ++j) {
+                const int U = __ldg(&lst[j]);
+                if (U < v.mask_lo) continue;
+                typename Traits<D>::Box b;
+                b.lo = a.nodebox[leaf0 + U].lo;
+                b.hi = a.nodebox[leaf0 + U].hi;
+                const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+                if (mk && v.leaf(U, mk, b)) return;
+            }
+        } else {
+            const typename Traits<D>::Box qb = v.query_box();
+            for (int j0 = 0; j0 < lc; j0 += 32) {
+                int U = -1, sol = 0;
+                int2 r = make_int2(0, 0);
+                bool cand = false;
+                if (j0 + lane < lc) {
+                    U = __ldg(&lst[j0 + lane]);
+                    if (U >= v.mask_lo) {
+                        typename Traits<D>::Box b;
+                        b.lo = a.nodebox[leaf0 + U].lo;
+                        b.hi = a.nodebox[leaf0 + U].hi;
+                        cand = NB<D>::bbox(qb, b) <= v.e2;
+                        // the records of all candidates in one lane-parallel load
+                        if (cand) {
+                            r = __ldg(&a.leafr[U]);
+                            if constexpr (V::NEEDS_SOLID) sol = a.lsolid[U];
+                        }
+                    }
+                }
+                unsigned cm = __ballot_sync(FULL, cand);
+                while (cm) {
+                    const int src = __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    const int Us = __shfl_sync(FULL, U, src);
+                    const int2 rs = make_int2(__shfl_sync(FULL, r.x, src), __shfl_sync(FULL, r.y, src));
+                    const int ss = V::NEEDS_SOLID ? __shfl_sync(FULL, sol, src) : 0;
+                    typename Traits<D>::Box b;
+                    b.lo = a.nodebox[leaf0 + Us].lo;
+                    b.hi = a.nodebox[leaf0 + Us].hi;
+                    const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+                    if (mk && v.leaf_rec(Us, mk, b, rs, ss)) return;
+                }
+            }
         }
         return;
     }
