@@ -127,6 +127,16 @@ __global__ void k_cellkey(const float* __restrict__ pts, int64_t n, GridParams g
     }
 }
 
+// The same packed for a keys-only sort: key << idx_bits | i in one word
+// (the caller checks that key bits + idx_bits <= 64 and n <= 2^idx_bits).
+template <int D>
+__global__ void k_cellkey_packed(const float* __restrict__ pts, int64_t n, GridParams g, int idx_bits,
+                                 uint64_t* __restrict__ words)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        words[i] = (cell_key<D>(pts + i * D, g) << idx_bits) | (uint64_t)i;
+}
+
 // ---------------------------------------------------------------------------
 // Density estimate for the automatic FDbscan / DenseBox choice: the share of
 // points that lie in DenseBox cells holding at least minPts points, from
@@ -241,6 +251,23 @@ __global__ void k_gather(const float* __restrict__ pts, const uint32_t* __restri
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         sp[i] = Traits<D>::load_point(pts, perm[i]);
+}
+
+// The same from sorted packed words, which it splits into the permutation
+// and the sorted keys.
+template <int D>
+__global__ void k_gather_packed(const float* __restrict__ pts, const uint64_t* __restrict__ words, int64_t n,
+                                int idx_bits, typename Traits<D>::Point* __restrict__ sp,
+                                uint32_t* __restrict__ perm, uint64_t* __restrict__ keys)
+{
+    const uint64_t mask = (1ull << idx_bits) - 1ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = words[i];
+        const uint32_t j = (uint32_t)(w & mask);
+        perm[i] = j;
+        keys[i] = w >> idx_bits;
+        sp[i] = Traits<D>::load_point(pts, j);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -573,6 +600,27 @@ void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, 
 #define CK_LAUNCH(D) k_cellkey<D><<<g, 256, 0, s>>>(pts, n, gp, keys, vals)
     GBD_DIM_SWITCH(dim, CK_LAUNCH)
 #undef CK_LAUNCH
+    note_launches(1);
+}
+
+void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParams& gp, int idx_bits,
+                           uint64_t* words, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+#define CKP_LAUNCH(D) k_cellkey_packed<D><<<g, 256, 0, s>>>(pts, n, gp, idx_bits, words)
+    GBD_DIM_SWITCH(dim, CKP_LAUNCH)
+#undef CKP_LAUNCH
+    note_launches(1);
+}
+
+void launch_gather_packed(const float* pts, const uint64_t* words, int64_t n, int dim, int idx_bits, void* sp,
+                          uint32_t* perm, uint64_t* keys, cudaStream_t s)
+{
+    const unsigned g = grid_for(n, 256, 152 * 16);
+#define GP_LAUNCH(D) \
+    k_gather_packed<D><<<g, 256, 0, s>>>(pts, words, n, idx_bits, static_cast<typename Traits<D>::Point*>(sp), perm, keys)
+    GBD_DIM_SWITCH(dim, GP_LAUNCH)
+#undef GP_LAUNCH
     note_launches(1);
 }
 

@@ -145,6 +145,12 @@ void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, 
 void launch_morton_generic(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* out,
                            cudaStream_t s);
 void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, cudaStream_t s);
+// DenseBox keys packed above the point index for a keys-only sort, and the
+// gather that splits the sorted words into permutation and keys
+void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParams& gp, int idx_bits,
+                           uint64_t* words, cudaStream_t s);
+void launch_gather_packed(const float* pts, const uint64_t* words, int64_t n, int dim, int idx_bits, void* sp,
+                          uint32_t* perm, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t n, int dim, int min_pts, float e2,
                                    const DenseBoxTemps& t, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
                                    cudaStream_t s);

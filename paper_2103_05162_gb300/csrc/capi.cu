@@ -483,17 +483,37 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
         int key_bits = 0;
         GridParams g = densebox_grid(lo, hi, dim, eps, g_tuning.cell_factor, &key_bits);
         uint64_t* k64 = static_cast<uint64_t*>(p.keys);
-        T.begin(ST_KEYS);
-        launch_cellkey(points, n, dim, g, k64, p.vals, s);
-        T.end();
-        T.begin(ST_SORT);
-        TRY_CUDA(sort_pairs_u64(k64, p.vals, n, key_bits, sb, s, &in_alt));
-        T.end();
-        const uint64_t* keys_sorted = in_alt ? static_cast<uint64_t*>(p.keys_alt) : k64;
-        perm = in_alt ? p.vals_alt : p.vals;
-        T.begin(ST_GATHER);
-        launch_gather(points, perm, n, dim, p.sp, s);
-        T.end();
+        uint64_t* k64_alt = static_cast<uint64_t*>(p.keys_alt);
+        int idx_bits = 1;
+        while (idx_bits < 32 && ((int64_t)1 << idx_bits) < n) ++idx_bits;
+        const uint64_t* keys_sorted;
+        if (key_bits + idx_bits <= 64) {
+            // cell key and point index in one word: a keys-only sort
+            T.begin(ST_KEYS);
+            launch_cellkey_packed(points, n, dim, g, idx_bits, k64, s);
+            T.end();
+            T.begin(ST_SORT);
+            TRY_CUDA(sort_keys_u64(k64, n, idx_bits, key_bits, sb, s, &in_alt));
+            T.end();
+            uint64_t* unpacked = in_alt ? k64 : k64_alt;
+            perm = p.vals;
+            T.begin(ST_GATHER);
+            launch_gather_packed(points, in_alt ? k64_alt : k64, n, dim, idx_bits, p.sp, p.vals, unpacked, s);
+            T.end();
+            keys_sorted = unpacked;
+        } else {
+            T.begin(ST_KEYS);
+            launch_cellkey(points, n, dim, g, k64, p.vals, s);
+            T.end();
+            T.begin(ST_SORT);
+            TRY_CUDA(sort_pairs_u64(k64, p.vals, n, key_bits, sb, s, &in_alt));
+            T.end();
+            keys_sorted = in_alt ? k64_alt : k64;
+            perm = in_alt ? p.vals_alt : p.vals;
+            T.begin(ST_GATHER);
+            launch_gather(points, perm, n, dim, p.sp, s);
+            T.end();
+        }
         T.begin(ST_LEAVES);
         TRY_CUDA(
             launch_densebox_leaves(keys_sorted, p.sp, n, dim, dense_mp, e2, p.db, p.leafr, p.lkey, p.ctrl, s));

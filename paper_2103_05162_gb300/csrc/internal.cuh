@@ -539,6 +539,11 @@ cudaError_t sort_pairs_u32(uint32_t* keys, uint32_t* vals, int64_t n, int bits, 
                            cudaStream_t s, bool* in_alt);
 cudaError_t sort_pairs_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
                            cudaStream_t s, bool* in_alt);
+// Keys only, by bits [shift0, shift0 + bits): for words key << shift0 | index
+// (distinct, so the order equals the stable order of the keys). The passes'
+// values buffers are not touched.
+cudaError_t sort_keys_u64(uint64_t* keys, int64_t n, int shift0, int bits, const SortBuffers& sb, cudaStream_t s,
+                          bool* in_alt);
 
 // scan.cu: out[i] = op(in[0..i]) (inclusive) or op(in[0..i-1]) (exclusive, out[0] = identity)
 enum ScanOp { SCAN_ADD = 0, SCAN_MAX = 1 };

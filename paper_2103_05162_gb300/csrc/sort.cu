@@ -10,7 +10,10 @@
 // the device error word instead of hanging.
 //
 // This orders Morton codes / grid-cell keys (the space-filling-curve order of
-// Sec. 4.1 and the cell grouping of Sec. 4.2).
+// Sec. 4.1 and the cell grouping of Sec. 4.2). A keys-only form sorts 64-bit
+// words that carry the key above the point's index (key << b | index) on
+// bits [b, b + key bits): a third less traffic per pass than separate
+// 64-bit keys and 32-bit values, in the same stable order.
 #include "internal.cuh"
 
 namespace gbd {
@@ -28,7 +31,7 @@ constexpr uint32_t FLAG_PRE = 2u << 30;
 constexpr uint32_t VAL_MASK = (1u << 30) - 1;
 
 template <typename K>
-__global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, int64_t n, int passes,
+__global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, int64_t n, int shift0, int passes,
                                                   uint32_t* __restrict__ hist)
 {
     __shared__ uint32_t sh[8 * RADIX];
@@ -36,7 +39,7 @@ __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, in
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS) {
         K k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (8 * p)) & 255u)], 1u);
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + 8 * p)) & 255u)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RADIX; i += THREADS) {
@@ -73,10 +76,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
     return r;
 }
 
-// (three blocks per SM: the compiler then keeps every key, value and rank in
-// 80 registers without spilling, instead of taking 128 and fitting two)
-template <typename K>
-__global__ void __launch_bounds__(THREADS, 3) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+// (three blocks per SM with values: the compiler then keeps every key, value
+// and rank in 80 registers without spilling, instead of taking 128 and
+// fitting two; four for keys only)
+template <typename K, bool VALS>
+__global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                       K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                                                       int shift, const uint32_t* __restrict__ hist,
                                                       uint32_t* __restrict__ status, uint32_t* tile_counter,
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_onesweep(const K* __restrict__ k
         int64_t idx = wbase + i * 32 + lane;
         if (idx < n) {
             k[i] = kin[idx];
-            v[i] = vin[idx];
+            v[i] = VALS ? vin[idx] : 0u;
         } else {
             k[i] = ~K(0);
             v[i] = 0;
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_onesweep(const K* __restrict__ k
     for (int i = 0; i < ITEMS; ++i) {
         if ((wbase + i * 32 + lane) < n) {
             keys_s[r[i]] = k[i];
-            vals_s[r[i]] = v[i];
+            if (VALS) vals_s[r[i]] = v[i];
         }
     }
     __syncthreads();
@@ -195,13 +199,14 @@ __global__ void __launch_bounds__(THREADS, 3) k_onesweep(const K* __restrict__ k
         const uint32_t d = (uint32_t)(kk >> shift) & 255u;
         const uint32_t o = s_gofs[d] + (uint32_t)j - s_excl[d];
         kout[o] = kk;
-        vout[o] = vals_s[j];
+        if (VALS) vout[o] = vals_s[j];
     }
 }
 
+// sorts by bits [shift0, shift0 + bits) of the keys; vals null: keys only
 template <typename K>
-cudaError_t sort_pairs(K* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb, cudaStream_t s,
-                       bool* in_alt)
+cudaError_t sort_pairs(K* keys, uint32_t* vals, int64_t n, int shift0, int bits, const SortBuffers& sb,
+                       cudaStream_t s, bool* in_alt)
 {
     *in_alt = false;
     if (n <= 1 || bits <= 0) return cudaSuccess;
@@ -213,21 +218,29 @@ cudaError_t sort_pairs(K* keys, uint32_t* vals, int64_t n, int bits, const SortB
     if ((e = cudaMemsetAsync(sb.status, 0, sizeof(uint32_t) * RADIX * (size_t)tiles * passes, s)) != cudaSuccess)
         return e;
     const int hist_blocks = (int)(tiles < 1216 ? tiles : 1216);
-    k_hist<K><<<hist_blocks, THREADS, 0, s>>>(keys, n, passes, sb.hist);
+    k_hist<K><<<hist_blocks, THREADS, 0, s>>>(keys, n, shift0, passes, sb.hist);
     note_launches(1);
-    const size_t smem = TILE_ITEMS * (sizeof(K) + sizeof(uint32_t));
+    const bool with_vals = vals != nullptr;
+    const size_t smem = TILE_ITEMS * (sizeof(K) + (with_vals ? sizeof(uint32_t) : 0));
     static_assert(TILE_ITEMS * sizeof(uint32_t) >= WARPS * RADIX * sizeof(uint32_t), "histograms alias keys");
-    if ((e = cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(with_vals ? k_onesweep<K, true> : k_onesweep<K, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     K* kin = keys;
     uint32_t* vin = vals;
     K* kout = static_cast<K*>(sb.keys_alt);
     uint32_t* vout = sb.vals_alt;
     for (int p = 0; p < passes; ++p) {
-        k_onesweep<K><<<(unsigned)tiles, THREADS, smem, s>>>(kin, vin, kout, vout, n, 8 * p, sb.hist + RADIX * p,
-                                                              sb.status + (size_t)RADIX * tiles * p,
-                                                              sb.counters + p, sb.err);
+        if (with_vals)
+            k_onesweep<K, true><<<(unsigned)tiles, THREADS, smem, s>>>(kin, vin, kout, vout, n, shift0 + 8 * p,
+                                                                       sb.hist + RADIX * p,
+                                                                       sb.status + (size_t)RADIX * tiles * p,
+                                                                       sb.counters + p, sb.err);
+        else
+            k_onesweep<K, false><<<(unsigned)tiles, THREADS, smem, s>>>(kin, nullptr, kout, nullptr, n,
+                                                                        shift0 + 8 * p, sb.hist + RADIX * p,
+                                                                        sb.status + (size_t)RADIX * tiles * p,
+                                                                        sb.counters + p, sb.err);
         note_launches(1);
         K* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
@@ -253,13 +266,19 @@ size_t sort_status_words(int64_t n, int key_bytes, int bits)
 cudaError_t sort_pairs_u32(uint32_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
                            cudaStream_t s, bool* in_alt)
 {
-    return sort_pairs<uint32_t>(keys, vals, n, bits, sb, s, in_alt);
+    return sort_pairs<uint32_t>(keys, vals, n, 0, bits, sb, s, in_alt);
 }
 
 cudaError_t sort_pairs_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,
                            cudaStream_t s, bool* in_alt)
 {
-    return sort_pairs<uint64_t>(keys, vals, n, bits, sb, s, in_alt);
+    return sort_pairs<uint64_t>(keys, vals, n, 0, bits, sb, s, in_alt);
+}
+
+cudaError_t sort_keys_u64(uint64_t* keys, int64_t n, int shift0, int bits, const SortBuffers& sb, cudaStream_t s,
+                          bool* in_alt)
+{
+    return sort_pairs<uint64_t>(keys, nullptr, n, shift0, bits, sb, s, in_alt);
 }
 
 }  // namespace gbd

@@ -115,6 +115,26 @@ def test_offset_coordinates_tiny_eps(algo):
             check(X, eps, mp, gb.MODE_DBSCAN, algo)
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_wide_cell_keys(d):
+    """DenseBox cells so small against the extent (about 1000 / 1e-7) that
+    the cell key takes (nearly) all 64 bits: the key cannot share a word with
+    the point index, so the pairs sort (key, index) runs instead of the
+    packed keys-only one. Exact duplicates make dense cells; a few points sit
+    one ulp (within eps) from another."""
+    rs = np.random.default_rng(11)
+    base = rs.integers(0, 1 << 10, size=(600, d)).astype(np.float32)
+    base[:, 0] = np.float32(0.5) + rs.integers(0, 2048, size=600).astype(np.float32) / np.float32(4096)
+    X = np.repeat(base, rs.integers(1, 12, size=600), axis=0)
+    near = X[:200].copy()
+    near[:, 0] = np.nextafter(near[:, 0], np.float32(2))
+    X = np.concatenate([X, near]).astype(np.float32)
+    rs.shuffle(X)
+    eps = float(np.spacing(np.float32(1)))
+    for mp in (2, 4, 9):
+        check(X, eps, mp, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX)
+
+
 @pytest.mark.parametrize("algo", ALGOS)
 def test_nonfinite_input_is_rejected(algo):
     X = blobs(1000, 3, 1)
