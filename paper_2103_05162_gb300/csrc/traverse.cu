@@ -1223,6 +1223,13 @@ __global__ void __launch_bounds__(INTRA_THREADS) k_intra(DevArgs<D> a)
         const int s = r.x, k = r.y - r.x;
         const TileParams tp = tile_params(a, (int)L);
         const bool valid = lane < k;
+        bool c = valid && a.core[s + lane];
+        if (tp.min_pts > 2 && !__any_sync(FULL, c)) {
+            // core flags known and none in the tile: no pair inside it
+            // unites or claims anything, and it is not solid
+            if (lane == 0) a.lsolid[L] = 0;
+            continue;
+        }
         const P p = a.sp[valid ? s + lane : s];
         // the tile's adjacency, two points at a time (packed)
         soa.put(lane, p);
@@ -1241,7 +1248,6 @@ __global__ void __launch_bounds__(INTRA_THREADS) k_intra(DevArgs<D> a)
             adj &= ~(1u << lane);
         }
         __syncwarp();
-        bool c = valid && a.core[s + lane];
         if (tp.min_pts == 2) {
             // no preprocessing: a neighbour inside the tile makes a point core
             // (neighbours in other tiles are found by the main phase)
