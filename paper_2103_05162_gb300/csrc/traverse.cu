@@ -777,6 +777,9 @@ struct MainBoxV {
     int lane;
     int sQ, eQ;
     typename T::Box qb;
+    // the cell's work can be split over `parts` warps: this one takes the
+    // neighbour leaves with L % parts == part
+    int part = 0, parts = 1;
 
     __device__ __forceinline__ void hits(const typename T::Node& n, bool& hl, bool& hr) const
     {
@@ -793,7 +796,7 @@ struct MainBoxV {
 
     __device__ bool leaf(int L, unsigned, const typename T::Box& box)
     {
-        if (L < mask_lo) return false;
+        if (L < mask_lo || L % parts != part) return false;
         const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
         if (lsolid[L]) {
@@ -1340,10 +1343,18 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
     uint32_t off = 0;
     for (int t = 0; t < KIND; ++t) off += a.ctrl[CTRL_KIND_COUNT + t];
     const int64_t cnt = a.ctrl[CTRL_KIND_COUNT + KIND];
+    // dense cells larger than a tile are few and each is much work: when
+    // there are more warps than cells, up to 8 warps share a cell (split by
+    // neighbour leaf), so that the launch is not as long as its largest cell
+    int parts = 1;
+    if (KIND == 2 && cnt > 0) {
+        const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+        parts = (int)max((int64_t)1, min((int64_t)8, warps / cnt));
+    }
     for (;;) {
         const int idx = next_leaf(&a.ctrl[CTRL_KIND_WORK + KIND]);
-        if (idx >= cnt) break;
-        const int L = a.klist[off + idx];
+        if (idx >= cnt * parts) break;
+        const int L = a.klist[off + idx / parts];
         const TileParams tp = tile_params(a, L);
         const bool listed = a.lcap > 0 && tp.min_pts > 2;
         const Rule rule{a.labels, a.core, tp.min_pts, a.mode == DBSCAN_MODE_DBSCAN && !listed};
@@ -1378,6 +1389,7 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
             MainBoxV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
             v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
+            v.part = idx % parts; v.parts = parts;
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
             walk(a, m, v, wm->stack, L);
