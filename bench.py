@@ -39,16 +39,22 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 # ----------------------------------------------------------------- bytes model
-def bytes_model(n: int, d: int, m: int, key_bytes: int) -> dict:
+def bytes_model(n: int, d: int, m: int, key_bytes: int, packed: bool = False) -> dict:
     """Compulsory device-memory traffic of each stage (each logical array read
     or written once per stage), in bytes per run. n points, d dims, m BVH
-    leaves, key_bytes 8 (DenseBox cell keys) or 4 (FDbscan Morton codes)."""
+    leaves, key_bytes 8 (DenseBox cell keys) or 4 (FDbscan Morton codes);
+    packed: DenseBox keys sorted as one 64-bit word with the point index,
+    which the gather splits into permutation and keys."""
     kv = key_bytes + 4
+    if packed:
+        keys, sort, gather = 4 * d * n + 8 * n, 16 * n, 8 * n + 8 * d * n + 12 * n
+    else:
+        keys, sort, gather = 4 * d * n + kv * n, 2 * kv * n, 4 * n + 8 * d * n
     return {
         "bounds": 4 * d * n,                              # read coordinates
-        "keys": 4 * d * n + kv * n,                       # read coordinates, write key + index
-        "sort": 2 * kv * n,                               # read and write (key, index) once
-        "gather": 4 * n + 4 * d * n + 4 * d * n,          # read index and coordinates, write sorted coordinates
+        "keys": keys,                                     # read coordinates, write key + index
+        "sort": sort,                                     # read and write (key, index) once
+        "gather": gather,                                 # read index and coordinates, write sorted coordinates
         "leaves": key_bytes * n + 5 * n + 8 * m,          # read keys, write flags, leaf records
         "lbvh": 4 * d * n + 8 * m + 64 * m + 64 * m,      # leaf boxes from points, keys, node records, refit
         "init": 5 * n,                                    # labels + core flags
@@ -58,21 +64,22 @@ def bytes_model(n: int, d: int, m: int, key_bytes: int) -> dict:
     }
 
 
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_pre_k_main_densebox_halos8m.md")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "preprocess_main_densebox_halos8m.md")
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2103_05162_gb300", "csrc", f)
                    for f in ("traverse.cu", "internal.cuh", "build.cuh")]
 
 
-def measured_traffic(n: int) -> float | None:
-    """DRAM bytes (read + write) of one k_pre launch on n points of the halo
-    workload (DenseBox, minPts 10), from the committed ncu summary, scaled by
-    the points; None if the summary is missing or the traversal sources have
-    changed since it was taken."""
+def measured_traffic(n: int, stage: str) -> float | None:
+    """DRAM bytes (read + write) of one run of a traversal stage
+    ("preprocess" or "main") on n points of the halo workload (DenseBox,
+    minPts 10), from the committed ncu summary, scaled by the points; None if
+    the summary is missing or the traversal sources have changed since it was
+    taken."""
     import hashlib
     import re
     try:
         text = open(TRAFFIC_SUMMARY).read()
-        per_point = float(re.search(r"^traffic_bytes_per_point:\s*([0-9.]+)", text, re.M).group(1))
+        per_point = float(re.search(r"^traffic_bytes_per_point_%s:\s*([0-9.]+)" % stage, text, re.M).group(1))
         want = re.search(r"^sources_sha256:\s*([0-9a-f]{64})", text, re.M).group(1)
         h = hashlib.sha256()
         for f in TRAFFIC_SOURCES:
@@ -284,19 +291,21 @@ def run_gb300(args, rank: int, world: int) -> None:
     # roofline of the dominant stage (its kernels timed with CUDA events on the
     # launching stream over the timed region)
     m = stats["leaves"]
-    model = bytes_model(n, d, m, 8 if algo == gb.ALGO_DENSEBOX else 4)
+    # DenseBox keys of the halo grid (3 x 12 bits) share a word with the index
+    model = bytes_model(n, d, m, 8 if algo == gb.ALGO_DENSEBOX else 4, packed=algo == gb.ALGO_DENSEBOX)
     stage_ms = {k: v[0] / max(1, args.steps) for k, v in prof.items() if v[1] > 0}
     top = max(stage_ms, key=stage_ms.get)
     peak, peak_kind = measured_peak_hbm()
     achieved = model[top] / (stage_ms[top] / 1e3) / 1e9
     path_bytes = sum(model[k] for k in stage_ms)
     traffic = None
-    if top == "preprocess" and algo == gb.ALGO_DENSEBOX and args.min_pts == 10:
-        traffic = measured_traffic(n)
+    if top in ("preprocess", "main") and algo == gb.ALGO_DENSEBOX and args.min_pts == 10:
+        traffic = measured_traffic(n, top)
+    kernels = {"preprocess": "k_pre + k_list_claims", "main": "k_intra + k_kinds_* + k_main x3"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_pre" if top == "preprocess" else top, "stage": top,
+                "traffic": traffic, "kernel": kernels.get(top, top), "stage": top,
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": model[top], "launch_ms": stage_ms[top],
-                "traffic_source": "profiles/k_pre_k_main_densebox_halos8m.md (8M capture scaled by points)"
+                "traffic_source": "profiles/preprocess_main_densebox_halos8m.md (8M capture scaled by points)"
                 if traffic is not None else None}
 
     cpu = None
