@@ -464,6 +464,7 @@ struct PreV {
                     mm &= mm - 1;
                     const P pq = NB<D>::shfl(p, q);
                     const unsigned h = __ballot_sync(FULL, in && dist2(pq, rp) <= e2);
+                    if (!h) continue;  // the common case in sparse regions: nothing to record
                     if (nlist) {
                         // each hit leaf point writes itself into q's list
                         const int at = __shfl_sync(FULL, nl, q) + __popc(h & ((1u << lane) - 1u));
