@@ -352,6 +352,13 @@ template <typename K>
 __device__ __forceinline__ bool radix_split_exceeds(const K* __restrict__ k, int64_t n, int64_t g, int T)
 {
     const int d = kdelta_t(k, n, g, g + 1);
+    // delta(g, j) does not grow as j moves away from g, so single probes
+    // decide most splits: T - 1 points on one side of g already in the run
+    // means more than T in all; fewer than T/2 - 1 on each side means at
+    // most T - 2
+    if (kdelta_t(k, n, g, g - (T - 1)) >= d || kdelta_t(k, n, g, g + T) >= d) return true;
+    const int h = T / 2 - 1;
+    if (kdelta_t(k, n, g, g - h) < d && kdelta_t(k, n, g, g + 1 + h) < d) return false;
     int64_t lo = g - T < 0 ? 0 : g - T, hi = g;  // smallest j in [lo, g] with delta(g, j) >= d
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
