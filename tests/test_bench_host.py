@@ -77,3 +77,48 @@ def test_max_over_ranks_gloo_world_2():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     del torch
+
+
+def _load_bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_measured_traffic_per_stage_and_source_check(tmp_path):
+    """The roofline's traffic comes from a profile summary per stage, scaled
+    by the points, and only while the sources still hash to the recorded
+    value."""
+    import hashlib
+    b = _load_bench()
+    srcs = []
+    for i, text in enumerate((b"kernel one\n", b"kernel two\n")):
+        f = tmp_path / f"src{i}.cu"
+        f.write_bytes(text)
+        srcs.append(str(f))
+    digest = hashlib.sha256(b"kernel one\nkernel two\n").hexdigest()
+    summary = tmp_path / "summary.md"
+    summary.write_text("# capture\n\ntraffic_bytes_per_point_preprocess: 45.5\n"
+                       "traffic_bytes_per_point_main: 22.25\nsources_sha256: %s\n" % digest)
+    b.TRAFFIC_SUMMARY, b.TRAFFIC_SOURCES = str(summary), srcs
+    assert b.measured_traffic(1000, "preprocess") == pytest.approx(45500.0)
+    assert b.measured_traffic(2000, "main") == pytest.approx(44500.0)
+    assert b.measured_traffic(1000, "sort") is None          # no figure for that stage
+    (tmp_path / "src1.cu").write_bytes(b"kernel two, changed\n")
+    assert b.measured_traffic(1000, "preprocess") is None    # sources changed since the capture
+
+
+def test_bytes_model_packed_sort_moves_a_third_less():
+    """Keys-only sort of packed 64-bit words: 16 bytes per point against 24
+    for (64-bit key, 32-bit index) pairs; the gather also writes the
+    permutation and the keys."""
+    b = _load_bench()
+    n, d, m = 1 << 20, 3, 1 << 15
+    pairs = b.bytes_model(n, d, m, 8)
+    packed = b.bytes_model(n, d, m, 8, packed=True)
+    assert pairs["sort"] == 24 * n and packed["sort"] == 16 * n
+    assert packed["gather"] - pairs["gather"] == 16 * n
+    assert {k: v for k, v in pairs.items() if k not in ("keys", "sort", "gather")} == \
+        {k: v for k, v in packed.items() if k not in ("keys", "sort", "gather")}
