@@ -292,23 +292,28 @@ dbscan_status dbscan_sort_pairs_u64(uint64_t* keys, uint32_t* values, int64_t n,
                                     dbscan_stream stream);
 
 /*
- * dbscan_sort_pairs_u64 for callers that cannot allocate device memory: code
- * that runs while a CUDA graph is being captured, real-time loops that must
- * not risk a cudaMalloc stall or failure, and applications whose device
- * memory belongs to a framework's pool. The paper has no counterpart; this is
- * an interface convenience of this library.
+ * dbscan_sort_pairs_u64 for callers that cannot allocate device memory. Some
+ * callers may not call cudaMalloc: a real-time loop, because an allocation
+ * can synchronise the device or fail at a moment the loop cannot absorb; an
+ * application or framework that hands all of the GPU's memory to its own
+ * pool or budget, so that memory taken behind the pool's back is not
+ * accounted for and can push the process out of memory. The paper has no
+ * counterpart; this is an interface convenience of this library.
  *   Same arguments, results and errors as dbscan_sort_pairs_u64, for
- *   n <= DBSCAN_SORT_NOALLOC_MAX_PAIRS (larger n: DBSCAN_ERR_INVALID_ARG).
+ *   n <= DBSCAN_SORT_NOALLOC_MAX_PAIRS (larger n: DBSCAN_ERR_INVALID_ARG,
+ *   nothing enqueued). The caller owns keys and values (device).
  *   Its scratch is a fixed static device array of about 14 MB, held by every
  *   GPU that loads the library until the process exits; the call makes no
  *   cudaMalloc/cudaFree or other allocating call.
- *   All calls share that array: calls that overlap on the GPU (other streams
- *   or host threads) race and must be serialised by the caller. Each call
- *   clears the parts that must start at zero.
- *   The first call on a device looks up the array's address
- *   (cudaGetSymbolAddress, with that device current): make it before any
- *   stream capture. Like dbscan_sort_pairs_u64 it waits for the stream at the
- *   end to report the sort's bounded-wait status.
+ *   All calls share that array and it keeps the last call's contents: each
+ *   call clears the parts that must start at zero. Calls that overlap on the
+ *   GPU (other streams or host threads) race on it and give wrong results;
+ *   the caller must serialise them.
+ *   The first call in each CUDA context of a device looks up the array's
+ *   address (cudaGetSymbolAddress, with that device current) and keeps it
+ *   for that context; make that first call before any stream capture. Like
+ *   dbscan_sort_pairs_u64 it waits for the stream at the end to report the
+ *   sort's bounded-wait status.
  */
 #define DBSCAN_SORT_NOALLOC_MAX_PAIRS (1 << 20)
 dbscan_status dbscan_sort_pairs_u64_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,

@@ -32,6 +32,8 @@ dbscan_status set_error(dbscan_status st, const char* fmt, ...)
     return st;
 }
 
+void clear_error() { t_err.clear(); }
+
 dbscan_status cuda_error(cudaError_t e, const char* what)
 {
     return set_error(e == cudaErrorMemoryAllocation ? DBSCAN_ERR_OOM : DBSCAN_ERR_CUDA, "%s: %s", what,

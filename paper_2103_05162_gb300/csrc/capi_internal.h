@@ -53,6 +53,8 @@ constexpr float DEFAULT_AUTO_OCCUPANCY = 16.0f;
 extern Tuning g_tuning;
 
 dbscan_status set_error(dbscan_status st, const char* fmt, ...);
+// empties this thread's dbscan_last_error() message (every entry point starts so)
+void clear_error();
 dbscan_status cuda_error(cudaError_t e, const char* what);
 dbscan_status check_run_args(const void* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
                              const void* labels_out);

@@ -1,10 +1,11 @@
 // dbscan_sort_pairs_u64_noalloc: the radix sort entry point for callers that
-// must not allocate device memory -- code running while a CUDA graph is being
-// captured, real-time loops where a cudaMalloc could stall or fail at the
-// wrong moment, and applications whose device memory is owned by a
-// framework-level pool. Its scratch (the alternate key/value buffers, the
-// digit histograms, the tile counters and the look-back status words) lives in
-// one file-scope __device__ array instead of a workspace from cudaMalloc.
+// must not allocate device memory -- real-time loops, where a cudaMalloc can
+// synchronise the device or fail at a moment the loop cannot absorb, and
+// applications whose device memory is handed to a framework-level pool or
+// budget that an allocation behind its back would overrun. Its scratch (the
+// alternate key/value buffers, the digit histograms, the tile counters and
+// the look-back status words) lives in one file-scope __device__ array
+// instead of a workspace from cudaMalloc.
 //
 // Costs and rules of use:
 //  * Every GPU that loads this library holds the array (NOALLOC_SCRATCH_BYTES,
@@ -14,10 +15,16 @@
 //    counters, status words, the error word) before sorting. Calls that
 //    overlap on the GPU (different streams, or different host threads) race
 //    on the array and give wrong results: serialise them.
-//  * The first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress (with that device current); make that first call
-//    before any stream capture.
+//  * In host code the array's name stands for a host-side shadow, not for
+//    device memory: the kernels get the device address, which the first call
+//    in each CUDA context looks up with cudaGetSymbolAddress (with that
+//    device current) and keeps for that context; make that first call before
+//    any stream capture.
+#include <cuda.h>
+
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "capi_internal.h"
 #include "internal.cuh"
@@ -41,25 +48,65 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_STATUS + align256(sizeof(uint32_t) 
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
-unsigned char* g_scratch_addr[MAX_DEVICES] = {};
+// device address of the array per (device, context id): a context created
+// after cudaDeviceReset loads the module anew, possibly elsewhere, and has a
+// new id, so a stale address is never reused
+std::map<std::pair<int, unsigned long long>, unsigned char*> g_scratch_addr;
 
-// device address of the scratch array on the current device (looked up once)
+// the unique id of the calling thread's current context (0: none current, or
+// the driver lacks cuCtxGetId); taken through the runtime's driver entry
+// points, so the library needs no link to libcuda
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// device address of the scratch array in the current device's context
+// (looked up once per context; looked up on every call if the context cannot
+// be identified)
 cudaError_t scratch_address(unsigned char** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    unsigned long long id = current_context_id();
+    if (id != 0) {
+        auto it = g_scratch_addr.find(std::make_pair(dev, id));
+        if (it != g_scratch_addr.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
     }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's primary context current if needed
+    if (e != cudaSuccess) return e;
+    id = current_context_id();
+    if (id != 0) g_scratch_addr[std::make_pair(dev, id)] = static_cast<unsigned char*>(p);
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
@@ -71,6 +118,7 @@ using namespace gbd;
 extern "C" dbscan_status dbscan_sort_pairs_u64_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
                                                        dbscan_stream stream)
 {
+    clear_error();
     if (n < 0 || n > NOALLOC_MAX_PAIRS)
         return set_error(DBSCAN_ERR_INVALID_ARG, "n = %lld is outside [0, %lld], the capacity of the static scratch",
                          (long long)n, (long long)NOALLOC_MAX_PAIRS);

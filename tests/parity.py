@@ -13,9 +13,10 @@ import numpy as np
 import oracle
 
 
-def assert_matches_oracle(X, eps, min_pts, mode, labels, core, ref=None):
-    """labels/core: numpy arrays from the CUDA path. Returns the oracle's
-    (labels, core) for reuse."""
+def assert_matches_oracle(X, eps, min_pts, mode, labels, core, ref=None, sets=None):
+    """labels/core: numpy arrays from the CUDA path. ``ref`` (the oracle's
+    (labels, core)) and ``sets`` (its border sets, ``oracle.border_sets``) are
+    computed when not given. Returns the oracle's (labels, core) for reuse."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     labels = np.asarray(labels, dtype=np.int64)
     core = np.asarray(core).astype(bool)
@@ -37,7 +38,7 @@ def assert_matches_oracle(X, eps, min_pts, mode, labels, core, ref=None):
     assert bad.size == 0, f"noise sets differ at {bad.size} points"
     border = np.nonzero(noncore & (olab >= 0))[0]
     if border.size:
-        off, sets = oracle.border_sets(X, eps, ocore, olab)
+        off, sets = oracle.border_sets(X, eps, ocore, olab) if sets is None else sets
         rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
         valid = rows * (1 << 32) + sets.astype(np.int64)
         got = border.astype(np.int64) * (1 << 32) + labels[border]

@@ -180,15 +180,6 @@ def test_uniform_2d_and_3d_many_tiles():
 
 # ----------------------------------------------------------------- full size
 
-@pytest.mark.slow
-@pytest.mark.parametrize("algo", ALGOS)
-def test_roads_4m_full_oracle(algo):
-    """The 2D workload at full size (4,194,304 points, eps 2e-4, minPts 10),
-    compared with the full oracle clustering."""
-    X = roads(1 << 22, 1)
-    check(X, 2e-4, 10, gb.MODE_DBSCAN, algo)
-
-
 @pytest.fixture(scope="module")
 def halos16m():
     n = 1 << 24

@@ -321,3 +321,50 @@ def test_distance_is_fp32_squared_form_without_fma():
             fma_witness += int(rounded != fused)
             exact_witness += int(rounded != exact)
     assert fma_witness > 0 and exact_witness > 0
+
+
+# ------------------------------------------------- per-point brute-force rows
+
+def _check_point_neighbors(X, eps, queries):
+    A = _adjacency(X, eps)
+    for q in queries:
+        q = int(q)
+        got = oracle.point_neighbors(X, eps, q)
+        want = np.nonzero(A[q])[0]
+        np.testing.assert_array_equal(got, want)
+        assert q in got  # x is its own neighbour (Sec. 2.1: N_eps(x) contains x)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_point_neighbors_matches_all_pairs_row(seed):
+    """point_neighbors (the checker of the sampled large-input tests) equals
+    the row of the independent numpy adjacency: blobs in 2D to 8D, the point
+    itself included, indices increasing."""
+    rs = np.random.default_rng(8000 + seed)
+    d = int(rs.integers(2, 9))
+    n = int(rs.integers(1, 600))
+    X = blobs(n, d, seed, n_blobs=3, sigma=0.03)
+    eps = float(np.float32(rs.uniform(0.02, 0.08) * np.sqrt(d)))
+    _check_point_neighbors(X, eps, rs.integers(0, n, size=min(n, 25)))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_point_neighbors_lattice_ties_duplicates_and_offsets(seed):
+    """Pairs exactly at distance eps (adjacent), at sqrt(2) eps (not),
+    duplicated points (distance 0), and coordinates near 1e3 whose
+    differences are rounded."""
+    rs = np.random.default_rng(8500 + seed)
+    d = 2 + seed % 2
+    X = rs.integers(0, 6, size=(int(rs.integers(20, 300)), d)).astype(np.float32)
+    X[1::7] = X[0]  # many copies of one point
+    _check_point_neighbors(X, 1.0, range(X.shape[0]))
+    Y = (1000.0 + rs.uniform(0, 0.05, size=(250, 3))).astype(np.float32)
+    _check_point_neighbors(Y, float(np.float32(0.004)), range(0, 250, 3))
+
+
+def test_point_neighbors_boundary_pair_and_isolated_point():
+    one_up = float(np.nextafter(np.float32(1.0), np.float32(2.0)))
+    X = np.array([[0, 0], [1, 0], [0, one_up], [5, 5]], dtype=np.float32)
+    assert oracle.point_neighbors(X, 1.0, 0).tolist() == [0, 1]
+    assert oracle.point_neighbors(X, 1.0, 2).tolist() == [2]
+    assert oracle.point_neighbors(X, 1.0, 3).tolist() == [3]
