@@ -86,21 +86,36 @@ typedef void* dbscan_stream;
  *   points      device, n*dim fp32, row-major (point i at points[i*dim..]).
  *   labels_out  device, n int32: canonical label or -1 (see above).
  *   core_out    device, n bytes (1 = core point) or NULL.
- * The call enqueues the whole pipeline on `stream`. It waits on the host once,
- * early, for the bounding box of the points (to size the grid and to report
- * DBSCAN_ERR_NONFINITE before any clustering work); everything after that is
- * asynchronous. A device-side timeout of the radix sort's bounded waits is
- * reported by the next call on the same stream or by dbscan_stream_status().
+ * The call enqueues the whole pipeline on `stream` and returns without
+ * waiting for the device (the grid of Sec. 4.2, the sort's key width and the
+ * automatic algorithm choice are all decided on the device). The caller keeps
+ * points and labels_out alive until the stream has finished the work. Argument
+ * errors are returned before anything is enqueued. The only host wait is the
+ * growth of the stream's workspace (the first call, or a larger n): it waits
+ * for the stream before reallocating. Errors found on the device -- a
+ * non-finite coordinate (DBSCAN_ERR_NONFINITE; labels_out is then not
+ * written) or a radix-sort wait that gave up (DBSCAN_ERR_DEVICE_TIMEOUT) --
+ * are reported by the next host sync point on the stream:
+ * dbscan_stream_status(), dbscan_run_host(), dbscan_run_sync().
  */
 dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int min_pts,
                          int mode, int algo, int32_t* labels_out, uint8_t* core_out,
                          dbscan_stream stream);
 
 /*
+ * dbscan_run, then a wait for `stream` and the run's device-side status:
+ * errors found on the device (above) are returned by this call.
+ */
+dbscan_status dbscan_run_sync(const float* points, int64_t n, int dim, float eps, int min_pts,
+                              int mode, int algo, int32_t* labels_out, uint8_t* core_out,
+                              dbscan_stream stream);
+
+/*
  * The same clustering on host buffers: copies points to the device, runs
  * dbscan_run, copies labels (and core flags if core_out != NULL) back and
- * waits for completion. Host buffers may be pageable or pinned (pinned is
- * faster). Uses a library-owned device staging area per stream.
+ * waits for completion; device-side errors of the run are returned. Host
+ * buffers may be pageable or pinned (pinned is faster). Uses a library-owned
+ * device staging area per stream.
  */
 dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts,
                               int mode, int algo, int32_t* labels_host, uint8_t* core_host,
@@ -207,9 +222,11 @@ dbscan_status dbscan_server_set_batching(dbscan_server* srv, int64_t max_job_poi
 dbscan_status dbscan_server_hold(dbscan_server* srv, int hold);
 dbscan_status dbscan_server_stats(dbscan_server* srv, int64_t* out4);
 
-/* Status of the last work enqueued by this library on `stream`: waits for the
- * stream, then returns DBSCAN_ERR_DEVICE_TIMEOUT if a bounded device-side
- * wait gave up (and clears the flag), else DBSCAN_OK. */
+/* Status of the work enqueued by this library on `stream` since the last
+ * status was taken: waits for the stream, then returns DBSCAN_ERR_NONFINITE if
+ * a run met a NaN or infinite coordinate, DBSCAN_ERR_DEVICE_TIMEOUT if a
+ * bounded device-side wait gave up (a run that met either wrote no labels),
+ * else DBSCAN_OK; clears the recorded errors. */
 dbscan_status dbscan_stream_status(dbscan_stream stream);
 
 /* Frees every cached device workspace (waits for their streams first). */
@@ -241,8 +258,9 @@ dbscan_status dbscan_set_auto_threshold(int dim, float dense_fraction, float occ
  * The algorithm the last clustering call on `stream` used (DBSCAN_ALGO_FDBSCAN
  * or DBSCAN_ALGO_DENSEBOX; -1 before any) and, if it was chosen automatically,
  * the estimates behind the choice in estimates_out[0..1]: the share of points
- * in dense cells and the mean cell occupancy (both -1 otherwise).
- * Host-side bookkeeping only: valid once that call has returned.
+ * in dense cells and the mean cell occupancy (both -1 otherwise). An
+ * automatic choice is made on the device: the call then waits for `stream`
+ * to read it.
  */
 dbscan_status dbscan_last_choice(dbscan_stream stream, int* algo_out, float* estimates_out);
 
@@ -270,6 +288,15 @@ const char* dbscan_profile_stage_name(int stage);
 
 /* Number of CUDA kernels this library has launched since it was loaded. */
 int64_t dbscan_kernel_launches(void);
+
+/* Test hooks of the radix sort's bounded look-back wait (the paper has no
+ * counterpart; they exist to exercise the timeout path without a fault):
+ * every later sort waits at most wait_limit polls (negative: the default,
+ * about 2^22 polls), and with stall_first_tile != 0 the first tile of each
+ * pass publishes nothing, so that every other tile's wait runs out. The sort
+ * then reports DBSCAN_ERR_DEVICE_TIMEOUT, its timed-out tiles write nothing,
+ * and no stage after it runs. Process-wide; restore with (-1, 0). */
+dbscan_status dbscan_test_sort_hooks(int64_t wait_limit, int stall_first_tile);
 
 /* Statistics of the last dbscan_run on `stream` (waits for it):
  * stats_out[0] = number of BVH leaves m, stats_out[1] = number of dense cells

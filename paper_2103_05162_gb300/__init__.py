@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
         sz = ctypes.c_size_t
         sig = {
             "dbscan_run": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
+            "dbscan_run_sync": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_host": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_batch": [vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp],
             "dbscan_run_multi": [vp, i64, i32, f32, vp, i32, i32, i32, vp, vp, vp],
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = True):
             "dbscan_profile_enable": [i32],
             "dbscan_profile_collect": [vp, vp, vp],
             "dbscan_last_stats": [vp, vp],
+            "dbscan_test_sort_hooks": [i64, i32],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -136,13 +138,15 @@ def _ptr(t):
 
 
 def dbscan_run(points, eps: float, min_pts: int, mode="dbscan", algo="densebox", labels_out=None,
-               core_out=None, want_core: bool = False, stream=None):
+               core_out=None, want_core: bool = False, stream=None, sync: bool = False):
     """Clusters ``points`` (a CUDA float32 tensor of shape (n, d), 2 <= d <= 8).
 
     Returns ``labels`` (int32, -1 = noise, else the smallest input index of a
     core point of the cluster) or ``(labels, core)`` when ``want_core`` or
     ``core_out`` is given. Work is enqueued on ``stream`` (default: the
-    current torch stream).
+    current torch stream) and the call returns without waiting for it;
+    errors found on the device (non-finite input, a bounded wait that gave
+    up) are raised by ``stream_status()``, or by this call with ``sync``.
     """
     import torch
     lib = load()
@@ -156,9 +160,10 @@ def dbscan_run(points, eps: float, min_pts: int, mode="dbscan", algo="densebox",
         labels_out = torch.empty(n, dtype=torch.int32, device=points.device)
     if core_out is None and want_core:
         core_out = torch.empty(n, dtype=torch.uint8, device=points.device)
+    fn = lib.dbscan_run_sync if sync else lib.dbscan_run
     with torch.cuda.device(points.device):
-        _check(lib.dbscan_run(_ptr(points), n, d, float(eps), int(min_pts), _mode(mode), _algo(algo),
-                              _ptr(labels_out), _ptr(core_out), _stream_handle(stream, points.device)))
+        _check(fn(_ptr(points), n, d, float(eps), int(min_pts), _mode(mode), _algo(algo),
+                  _ptr(labels_out), _ptr(core_out), _stream_handle(stream, points.device)))
     return (labels_out, core_out) if core_out is not None else labels_out
 
 
@@ -393,6 +398,12 @@ def last_stats(stream=None) -> dict:
     out = (ctypes.c_int64 * 2)()
     _check(load().dbscan_last_stats(_stream_handle(stream), out))
     return {"leaves": int(out[0]), "dense_cells": int(out[1])}
+
+
+def test_sort_hooks(wait_limit: int = -1, stall_first_tile: bool = False):
+    """Test hooks of the radix sort's bounded wait (see dbscan_test_sort_hooks);
+    (-1, False) restores the defaults."""
+    _check(load().dbscan_test_sort_hooks(int(wait_limit), 1 if stall_first_tile else 0))
 
 
 def set_tuning(block_size: int = 0, cell_factor: float = 0.0):

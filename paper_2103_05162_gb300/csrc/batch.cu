@@ -117,8 +117,9 @@ __global__ void k_bkeys(const int64_t* __restrict__ offs,
 
 __global__ void k_bgather(const int64_t* __restrict__ offs,
                           const InstDev* __restrict__ inst, int count, const uint32_t* __restrict__ perm, int64_t n,
-                          float4* __restrict__ sp)
+                          float4* __restrict__ sp, const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;  // a sort that gave up: stale permutation words
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = perm[i];
         sp[i] = load_row(inst[find_inst(offs, count, row)], row);
@@ -132,6 +133,7 @@ __global__ void k_bdense_classify(const uint64_t* __restrict__ keys, const float
                                   int32_t* __restrict__ dstart, uint32_t* __restrict__ ctrl)
 {
     using T = Traits<3>;
+    if (!stage_on(ctrl, -1)) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; base < n; base += stride) {
@@ -196,8 +198,9 @@ __global__ void k_inst_roots(const int2* __restrict__ range, const int32_t* __re
 
 __global__ void k_binit(const uint64_t* __restrict__ keys, int lb, const InstDev* __restrict__ inst,
                         const uint8_t* __restrict__ pdense, const int32_t* __restrict__ dstart, int64_t n,
-                        int32_t* __restrict__ labels, uint8_t* __restrict__ core)
+                        int32_t* __restrict__ labels, uint8_t* __restrict__ core, const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;  // a sort that gave up: stale keys would index past the instances
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (pdense && pdense[i]) {
             labels[i] = dstart[i];
@@ -213,8 +216,9 @@ __global__ void k_binit(const uint64_t* __restrict__ keys, int lb, const InstDev
 // per root
 __global__ void k_bfinalize(int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
                             const uint64_t* __restrict__ keys, int lb, const InstDev* __restrict__ inst, int64_t n,
-                            int32_t* __restrict__ canon)
+                            int32_t* __restrict__ canon, const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
         const int64_t i = base + (threadIdx.x & 31);
@@ -228,8 +232,9 @@ __global__ void k_bfinalize(int32_t* labels, const uint8_t* __restrict__ core, c
 // outputs of every instance, in its own buffers (instance-relative labels)
 __global__ void k_brelabel(const int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
                            const uint64_t* __restrict__ keys, int lb, const InstDev* __restrict__ inst, int64_t n,
-                           int mode, const int32_t* __restrict__ canon)
+                           int mode, const int32_t* __restrict__ canon, const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;  // aborted batch: nothing is written
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const bool c = core[i] != 0;
         const int r = uf_root(labels, (int)i);
@@ -405,12 +410,13 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     sb.hist = p.hist;
     sb.status = p.status;
     sb.counters = p.counters;
-    sb.err = p.ctrl + CTRL_ERR;
+    sb.err = p.ctrl + CTRL_ABORT;  // a wait that runs out stops every later stage
+    sb.ctl.abort = p.ctrl + CTRL_ABORT;
     bool in_alt = false;
     if ((e = sort_pairs_u64(p.keys, p.vals, n, key_bits, sb, s, &in_alt)) != cudaSuccess) return e;
     const uint64_t* keys = in_alt ? p.keys_alt : p.keys;
     const uint32_t* perm = in_alt ? p.vals_alt : p.vals;
-    k_bgather<<<grid_n(n), 256, 0, s>>>(p.offs, p.inst, count, perm, n, p.sp);
+    k_bgather<<<grid_n(n), 256, 0, s>>>(p.offs, p.inst, count, perm, n, p.sp, p.ctrl);
     note_launches(1);
     if (algo == DBSCAN_ALGO_DENSEBOX) {
         if ((e = cudaMemsetAsync(p.db.pdense, 0, (size_t)n, s)) != cudaSuccess) return e;
@@ -425,7 +431,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     if ((e = cudaMemsetAsync(p.ctrl + CTRL_WORK_PRE, 0, (CTRL_WORK_END - CTRL_WORK_PRE) * sizeof(uint32_t), s)) !=
         cudaSuccess)
         return e;
-    k_binit<<<grid_n(n), 256, 0, s>>>(keys, lb, p.inst, p.db.pdense, p.db.dstart, n, p.labels, p.core);
+    k_binit<<<grid_n(n), 256, 0, s>>>(keys, lb, p.inst, p.db.pdense, p.db.dstart, n, p.labels, p.core, p.ctrl);
     note_launches(1);
     if ((e = cudaMemsetAsync(p.canon, 0x7f, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) return e;
     ClusterArgs a;
@@ -466,8 +472,8 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     if ((e = launch_cluster_starts(a, s)) != cudaSuccess) return e;
     if ((e = launch_cluster_pre(a, s)) != cudaSuccess) return e;
     if ((e = launch_cluster_main(a, s)) != cudaSuccess) return e;
-    k_bfinalize<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, p.canon);
-    k_brelabel<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, mode, p.canon);
+    k_bfinalize<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, p.canon, p.ctrl);
+    k_brelabel<<<grid_n(n), 256, 0, s>>>(p.labels, p.core, perm, keys, lb, p.inst, n, mode, p.canon, p.ctrl);
     note_launches(2);
     return cudaGetLastError();
 }
@@ -523,6 +529,8 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
     BTRY(cudaMemcpyAsync(p.offs, offsets, sizeof(int64_t) * ((size_t)count + 1), cudaMemcpyHostToDevice, s));
     BTRY(cudaMemcpyAsync(p.inst, inst.data(), sizeof(InstDev) * (size_t)count, cudaMemcpyHostToDevice, s));
     BTRY(cudaMemcpyAsync(p.bounds, hb.data(), sizeof(uint32_t) * hb.size(), cudaMemcpyHostToDevice, s));
+    // fold the last run's abort bits into the error word and clear them
+    launch_run_begin(p.ctrl, algo, s);
     k_bbounds<<<grid_n(n), 256, 0, s>>>(p.offs, p.inst, count, n, p.bounds, p.bounds + 6 * (size_t)count);
     note_launches(1);
     uint32_t err = 0;

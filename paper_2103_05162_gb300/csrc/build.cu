@@ -40,7 +40,59 @@ __global__ void __launch_bounds__(BT) k_bounds(const float* __restrict__ pts, in
         atomicMin(&ctrl[CTRL_LO + threadIdx.x], s_lo[threadIdx.x]);
         atomicMax(&ctrl[CTRL_HI + threadIdx.x], s_hi[threadIdx.x]);
     }
-    if (threadIdx.x == 0 && s_bad) atomicOr(&ctrl[CTRL_NONFINITE], 1u);
+    if (threadIdx.x == 0 && s_bad) atomicOr(&ctrl[CTRL_ABORT], ERR_NONFINITE);
+}
+
+// the run's first kernel (see launch_run_begin)
+__global__ void k_run_begin(uint32_t* ctrl, int algo)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const uint32_t a = ctrl[CTRL_ABORT];
+        if (a) ctrl[CTRL_ERR] |= a;
+        ctrl[CTRL_ABORT] = 0u;
+        ctrl[CTRL_ALGO] = (uint32_t)algo;
+    }
+}
+
+// DenseBox grid (Sec. 4.2) from the bounds on the device, in double
+// precision: cell side h = f * eps / sqrt(D), enlarged when the widest axis
+// would need more than 2^max_axis_bits - 2 cells (the per-cell guard keeps
+// the result exact for any cell size, reading of Sec. 4.2); cmax_k = the
+// cell index of hi_k (plus one spare cell for rounding at the top); the key
+// interleaves `bits` bits per axis, enough for every cmax_k.
+template <int D>
+__global__ void k_grid(uint32_t* ctrl, float eps, float factor, int max_axis_bits, GridParams* gp)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GridParams g{};
+    double h = (double)factor * (double)eps / sqrt((double)D);
+    const double maxcells = ldexp(1.0, max_axis_bits);
+    float lo[D], hi[D];
+    double ext_max = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        lo[k] = ord2f(ctrl[CTRL_LO + k]);
+        hi[k] = ord2f(ctrl[CTRL_HI + k]);
+        ext_max = fmax(ext_max, (double)hi[k] - (double)lo[k]);
+    }
+    if (!(ext_max >= 0.0) || isinf(ext_max)) ext_max = 0.0;  // non-finite input: the run is aborted anyway
+    if (ext_max / h >= maxcells - 2.0) h = ext_max / (maxcells - 2.0);
+    const float inv_h = (float)(1.0 / h);
+    int bits = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        g.lo[k] = lo[k];
+        double c = floor(((double)hi[k] - (double)lo[k]) * (double)inv_h) + 1.0;
+        if (!(c >= 1.0)) c = 1.0;
+        if (c > maxcells - 1.0) c = maxcells - 1.0;
+        g.cmax[k] = (uint32_t)c;
+        while (bits < max_axis_bits && (ldexp(1.0, bits) - 1.0) < (double)g.cmax[k]) ++bits;
+    }
+    g.inv_h = inv_h;
+    g.bits = bits;
+    g.morton = 1;
+    *gp = g;
+    ctrl[CTRL_KEYBITS] = (uint32_t)(bits * D);
 }
 
 // ---------------------------------------------------------------------------
@@ -52,6 +104,7 @@ template <int D>
 __global__ void k_morton32(const float* __restrict__ pts, int64_t n, const uint32_t* __restrict__ ctrl, int bits,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
+    if (!stage_on(ctrl, DBSCAN_ALGO_FDBSCAN)) return;
     float lo[D], scale[D];
     const float cells = (float)(1u << bits);
 #pragma unroll
@@ -77,6 +130,7 @@ template <int D>
 __global__ void k_morton64(const float* __restrict__ pts, int64_t n, const uint32_t* __restrict__ ctrl, int bits,
                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
+    if (!stage_on(ctrl, DBSCAN_ALGO_FDBSCAN)) return;
     float lo[D], scale[D];
     const float cells = (float)(1u << bits);
 #pragma unroll
@@ -117,22 +171,19 @@ __device__ __forceinline__ uint64_t cell_key(const float* __restrict__ p, const 
     return key;
 }
 
+// Packed for a keys-only sort: key << idx_bits | i in one word (the host
+// caps the grid so that key bits + idx_bits <= 64, and n <= 2^idx_bits). The
+// words go to the buffer the sort takes its input from (sort_dev_input_alt).
 template <int D>
-__global__ void k_cellkey(const float* __restrict__ pts, int64_t n, GridParams g, uint64_t* __restrict__ keys,
-                          uint32_t* __restrict__ vals)
+__global__ void k_cellkey_packed(const float* __restrict__ pts, int64_t n, const GridParams* __restrict__ gp,
+                                 const uint32_t* __restrict__ ctrl, int idx_bits, int host_passes,
+                                 uint64_t* __restrict__ words0, uint64_t* __restrict__ words1)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        keys[i] = cell_key<D>(pts + i * D, g);
-        vals[i] = (uint32_t)i;
-    }
-}
-
-// The same packed for a keys-only sort: key << idx_bits | i in one word
-// (the caller checks that key bits + idx_bits <= 64 and n <= 2^idx_bits).
-template <int D>
-__global__ void k_cellkey_packed(const float* __restrict__ pts, int64_t n, GridParams g, int idx_bits,
-                                 uint64_t* __restrict__ words)
-{
+    if (!stage_on(ctrl, DBSCAN_ALGO_DENSEBOX)) return;
+    const GridParams g = *gp;
+    // (host_passes 0: no sort runs, n <= 1, and the words stay in words0)
+    uint64_t* __restrict__ words =
+        host_passes > 0 && sort_dev_input_alt(host_passes, sort_passes((int)ctrl[CTRL_KEYBITS])) ? words1 : words0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         words[i] = (cell_key<D>(pts + i * D, g) << idx_bits) | (uint64_t)i;
 }
@@ -156,9 +207,12 @@ __device__ __forceinline__ uint32_t est_hash(uint64_t k)
 }
 
 template <int D>
-__global__ void k_est_insert(const float* __restrict__ pts, int64_t n, int s, GridParams g,
-                             unsigned long long* __restrict__ table, int32_t* __restrict__ slot)
+__global__ void k_est_insert(const float* __restrict__ pts, int64_t n, int s, const GridParams* __restrict__ gp,
+                             const uint32_t* __restrict__ ctrl, unsigned long long* __restrict__ table,
+                             int32_t* __restrict__ slot)
 {
+    if (!stage_on(ctrl, -1)) return;
+    const GridParams g = *gp;
     for (int j = threadIdx.x; j < s; j += blockDim.x) {
         const int64_t i = (int64_t)j * n / s;
         const unsigned long long key = cell_key<D>(pts + i * D, g);
@@ -176,9 +230,12 @@ __global__ void k_est_insert(const float* __restrict__ pts, int64_t n, int s, Gr
 }
 
 template <int D>
-__global__ void k_est_count(const float* __restrict__ pts, int64_t n, int64_t stride, GridParams g,
+__global__ void k_est_count(const float* __restrict__ pts, int64_t n, int64_t stride,
+                            const GridParams* __restrict__ gp, const uint32_t* __restrict__ ctrl,
                             const unsigned long long* __restrict__ table, uint32_t* __restrict__ counts)
 {
+    if (!stage_on(ctrl, -1)) return;
+    const GridParams g = *gp;
     __shared__ uint32_t sc[EST_SLOTS];
     for (int t = threadIdx.x; t < EST_SLOTS; t += blockDim.x) sc[t] = 0;
     __syncthreads();
@@ -201,11 +258,16 @@ __global__ void k_est_count(const float* __restrict__ pts, int64_t n, int64_t st
         if (sc[t]) atomicAdd(&counts[t], sc[t]);
 }
 
-// out[0] = samples whose cell holds >= min_pts points; out[1..2] = the sum
-// over the samples of their cell's point count (64-bit, low word first)
+// out[0] = samples whose cell holds >= min_pts points; out[2..3] = the sum
+// over the samples of their cell's point count (64-bit, low word first);
+// then the choice: DenseBox if the dense share reaches auto_fraction or the
+// mean occupancy auto_occupancy, else FDbscan (CTRL_ALGO, estimates in
+// CTRL_EST_FRAC / CTRL_EST_OCC). One block.
 __global__ void k_est_result(const int32_t* __restrict__ slot, int s, const uint32_t* __restrict__ counts,
-                             int64_t n, int64_t stride, int min_pts, uint32_t* __restrict__ out)
+                             int64_t n, int64_t stride, int min_pts, float auto_fraction, float auto_occupancy,
+                             uint32_t* __restrict__ out, uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;
     uint32_t c = 0;
     unsigned long long occ = 0;
     for (int j = threadIdx.x; j < s; j += blockDim.x) {
@@ -222,6 +284,18 @@ __global__ void k_est_result(const int32_t* __restrict__ slot, int s, const uint
     }
     atomicAdd(out, c);
     atomicAdd(reinterpret_cast<unsigned long long*>(out + 2), occ);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence_block();
+        const uint32_t dense = *(volatile uint32_t*)out;
+        const unsigned long long occ_sum = *(volatile unsigned long long*)(out + 2);
+        const float frac = (float)dense / (float)s;
+        const float mean_occ = (float)((double)occ_sum / (double)s);
+        ctrl[CTRL_EST_FRAC] = __float_as_uint(frac);
+        ctrl[CTRL_EST_OCC] = __float_as_uint(mean_occ);
+        ctrl[CTRL_ALGO] = (frac >= auto_fraction || mean_occ >= auto_occupancy) ? (uint32_t)DBSCAN_ALGO_DENSEBOX
+                                                                               : (uint32_t)DBSCAN_ALGO_FDBSCAN;
+    }
 }
 
 // generic Morton codes with host-side bounds (component entry point)
@@ -247,8 +321,10 @@ __global__ void k_morton_generic(const float* __restrict__ pts, int64_t n, GridP
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void k_gather(const float* __restrict__ pts, const uint32_t* __restrict__ perm, int64_t n,
-                         typename Traits<D>::Point* __restrict__ sp)
+                         typename Traits<D>::Point* __restrict__ sp, const uint32_t* __restrict__ ctrl, int algo)
 {
+    // a sort that gave up leaves stale words in perm: never index with them
+    if (!stage_on(ctrl, algo)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         sp[i] = Traits<D>::load_point(pts, perm[i]);
 }
@@ -258,8 +334,10 @@ __global__ void k_gather(const float* __restrict__ pts, const uint32_t* __restri
 template <int D>
 __global__ void k_gather_packed(const float* __restrict__ pts, const uint64_t* __restrict__ words, int64_t n,
                                 int idx_bits, typename Traits<D>::Point* __restrict__ sp,
-                                uint32_t* __restrict__ perm, uint64_t* __restrict__ keys)
+                                uint32_t* __restrict__ perm, uint64_t* __restrict__ keys,
+                                const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, DBSCAN_ALGO_DENSEBOX)) return;  // (a sort that gave up: stale index bits)
     const uint64_t mask = (1ull << idx_bits) - 1ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t w = words[i];
@@ -291,6 +369,7 @@ __global__ void k_dense_classify(const uint64_t* __restrict__ keys, const typena
                                  int32_t* __restrict__ dstart, uint32_t* __restrict__ ctrl)
 {
     using T = Traits<D>;
+    if (!stage_on(ctrl, DBSCAN_ALGO_DENSEBOX)) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // whole warps iterate together so that the cell walks below are cooperative
@@ -383,8 +462,9 @@ __device__ __forceinline__ bool radix_split_exceeds(const K* __restrict__ k, int
 template <typename K>
 __global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ dstart,
                              const uint8_t* __restrict__ pdense, int64_t n, int T, int id_shift,
-                             int32_t* __restrict__ lf)
+                             int32_t* __restrict__ lf, const uint32_t* __restrict__ ctrl, int algo)
 {
+    if (!stage_on(ctrl, algo)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int f;
         if (i == 0) f = 1;
@@ -398,8 +478,11 @@ __global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restri
 
 // lidx = exclusive scan of lf; writes leaf starts and m
 __global__ void k_leaf_write(const int32_t* __restrict__ lf, const int32_t* __restrict__ lidx, int64_t n,
-                             int32_t* __restrict__ lstart, uint32_t* __restrict__ ctrl)
+                             int32_t* __restrict__ lstart, uint32_t* __restrict__ ctrl, int algo)
 {
+    // skipped (aborted run, or the other algorithm's chain): m stays 0 and
+    // every later stage finds no leaves
+    if (!stage_on(ctrl, algo)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (lf[i]) lstart[lidx[i]] = (int32_t)i;
         if (i == n - 1) {
@@ -414,8 +497,10 @@ __global__ void k_leaf_write(const int32_t* __restrict__ lf, const int32_t* __re
 template <typename K>
 __global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t* __restrict__ pdense,
                                const K* __restrict__ keys, const uint32_t* __restrict__ ctrl, int id_shift,
-                               int2* __restrict__ leafr, uint64_t* __restrict__ lkey, int32_t* __restrict__ linst)
+                               int2* __restrict__ leafr, uint64_t* __restrict__ lkey, int32_t* __restrict__ linst,
+                               int algo)
 {
+    if (!stage_on(ctrl, algo)) return;
     const int64_t m = ctrl[CTRL_M];
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = lstart[l], e = lstart[l + 1];
@@ -541,8 +626,9 @@ __global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, const GridParams& g, int min_pts,
-                                   const EstBuffers& eb, cudaStream_t s)
+cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, const GridParams* g, int min_pts,
+                                   float auto_fraction, float auto_occupancy, const EstBuffers& eb, uint32_t* ctrl,
+                                   cudaStream_t s)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(eb.table, 0xff, sizeof(unsigned long long) * EST_SLOTS, s)) != cudaSuccess) return e;
@@ -554,12 +640,13 @@ cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, con
     if (gb > 152 * 4) gb = 152 * 4;
 #define EST_LAUNCH(D)                                                                      \
     do {                                                                                   \
-        k_est_insert<D><<<1, 1024, 0, s>>>(points, n, smp, g, eb.table, eb.slot);         \
-        k_est_count<D><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, eb.table, eb.counts); \
+        k_est_insert<D><<<1, 1024, 0, s>>>(points, n, smp, g, ctrl, eb.table, eb.slot);   \
+        k_est_count<D><<<(unsigned)gb, 256, 0, s>>>(points, n, stride, g, ctrl, eb.table, eb.counts); \
     } while (0)
     GBD_DIM_SWITCH(dim, EST_LAUNCH)
 #undef EST_LAUNCH
-    k_est_result<<<1, 1024, 0, s>>>(eb.slot, smp, eb.counts, n, stride, min_pts, eb.result);
+    k_est_result<<<1, 1024, 0, s>>>(eb.slot, smp, eb.counts, n, stride, min_pts, auto_fraction, auto_occupancy,
+                                    eb.result, ctrl);
     note_launches(3);
     return cudaGetLastError();
 }
@@ -578,6 +665,21 @@ void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStr
     k_bounds<D><<<grid_for(n * D, bounds_threads<D>(), 152 * 8), bounds_threads<D>(), 0, s>>>(pts, n, ctrl)
     GBD_DIM_SWITCH(dim, BOUNDS_LAUNCH)
 #undef BOUNDS_LAUNCH
+    note_launches(1);
+}
+
+void launch_run_begin(uint32_t* ctrl, int algo, cudaStream_t s)
+{
+    k_run_begin<<<1, 32, 0, s>>>(ctrl, algo);
+    note_launches(1);
+}
+
+void launch_grid(uint32_t* ctrl, int dim, float eps, float factor, int max_axis_bits, GridParams* gp,
+                 cudaStream_t s)
+{
+#define GRID_LAUNCH(D) k_grid<D><<<1, 32, 0, s>>>(ctrl, eps, factor, max_axis_bits, gp)
+    GBD_DIM_SWITCH(dim, GRID_LAUNCH)
+#undef GRID_LAUNCH
     note_launches(1);
 }
 
@@ -600,32 +702,24 @@ void launch_morton64(const float* pts, int64_t n, int dim, const uint32_t* ctrl,
     note_launches(1);
 }
 
-void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* keys, uint32_t* vals,
-                    cudaStream_t s)
+void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParams* gp, const uint32_t* ctrl,
+                           int idx_bits, int host_passes, uint64_t* words0, uint64_t* words1, cudaStream_t s)
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
-#define CK_LAUNCH(D) k_cellkey<D><<<g, 256, 0, s>>>(pts, n, gp, keys, vals)
-    GBD_DIM_SWITCH(dim, CK_LAUNCH)
-#undef CK_LAUNCH
-    note_launches(1);
-}
-
-void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParams& gp, int idx_bits,
-                           uint64_t* words, cudaStream_t s)
-{
-    const unsigned g = grid_for(n, 256, 152 * 16);
-#define CKP_LAUNCH(D) k_cellkey_packed<D><<<g, 256, 0, s>>>(pts, n, gp, idx_bits, words)
+#define CKP_LAUNCH(D) \
+    k_cellkey_packed<D><<<g, 256, 0, s>>>(pts, n, gp, ctrl, idx_bits, host_passes, words0, words1)
     GBD_DIM_SWITCH(dim, CKP_LAUNCH)
 #undef CKP_LAUNCH
     note_launches(1);
 }
 
 void launch_gather_packed(const float* pts, const uint64_t* words, int64_t n, int dim, int idx_bits, void* sp,
-                          uint32_t* perm, uint64_t* keys, cudaStream_t s)
+                          uint32_t* perm, uint64_t* keys, const uint32_t* ctrl, cudaStream_t s)
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
-#define GP_LAUNCH(D) \
-    k_gather_packed<D><<<g, 256, 0, s>>>(pts, words, n, idx_bits, static_cast<typename Traits<D>::Point*>(sp), perm, keys)
+#define GP_LAUNCH(D)                                                                                         \
+    k_gather_packed<D><<<g, 256, 0, s>>>(pts, words, n, idx_bits, static_cast<typename Traits<D>::Point*>(sp), perm, \
+                                         keys, ctrl)
     GBD_DIM_SWITCH(dim, GP_LAUNCH)
 #undef GP_LAUNCH
     note_launches(1);
@@ -639,10 +733,12 @@ void launch_morton_generic(const float* pts, int64_t n, int dim, const GridParam
     note_launches(1);
 }
 
-void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, cudaStream_t s)
+void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, const uint32_t* ctrl,
+                   int algo, cudaStream_t s)
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
-#define GATHER_LAUNCH(D) k_gather<D><<<g, 256, 0, s>>>(pts, perm, n, static_cast<typename Traits<D>::Point*>(sp))
+#define GATHER_LAUNCH(D) \
+    k_gather<D><<<g, 256, 0, s>>>(pts, perm, n, static_cast<typename Traits<D>::Point*>(sp), ctrl, algo)
     GBD_DIM_SWITCH(dim, GATHER_LAUNCH)
 #undef GATHER_LAUNCH
     note_launches(1);
@@ -661,10 +757,11 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
                                           t.pdense, t.dstart, ctrl)
     GBD_DIM_SWITCH(dim, DC_LAUNCH)
 #undef DC_LAUNCH
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, 64, t.lf);
+    const int A = DBSCAN_ALGO_DENSEBOX;
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, 64, t.lf, ctrl, A);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, 64, leafr, lkey, nullptr);
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, 64, leafr, lkey, nullptr, A);
     note_launches(4);
     return cudaGetLastError();
 }
@@ -677,10 +774,10 @@ cudaError_t launch_batch_leaves(const uint64_t* keys, int64_t n, int id_shift, c
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, id_shift, t.lf);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, id_shift, t.lf, ctrl, -1);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, id_shift, leafr, lkey, linst);
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, -1);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, id_shift, leafr, lkey, linst, -1);
     note_launches(3);
     return cudaGetLastError();
 }
@@ -690,10 +787,11 @@ cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBox
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, TILE, 64, t.lf);
+    const int A = DBSCAN_ALGO_FDBSCAN;
+    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, TILE, 64, t.lf, ctrl, A);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, 64, leafr, lkey, nullptr);
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
+    k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, 64, leafr, lkey, nullptr, A);
     note_launches(3);
     return cudaGetLastError();
 }
@@ -703,10 +801,11 @@ cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBox
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, nullptr, nullptr, n, TILE, 64, t.lf);
+    const int A = DBSCAN_ALGO_FDBSCAN;
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, nullptr, nullptr, n, TILE, 64, t.lf, ctrl, A);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl);
-    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys, ctrl, 64, leafr, lkey, nullptr);
+    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
+    k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys, ctrl, 64, leafr, lkey, nullptr, A);
     note_launches(3);
     return cudaGetLastError();
 }

@@ -37,8 +37,8 @@ inline int fdbscan_bits(int dim)
 
 // Slots of the per-workspace control block (uint32 words in device memory).
 enum : int {
-    CTRL_NONFINITE = 8,  // nonzero if a coordinate is NaN/Inf
-    CTRL_ERR = 9,        // device error bits (ERR_*)
+    CTRL_NONFINITE = 8,  // nonzero if a coordinate is NaN/Inf (batches)
+    CTRL_ERR = 9,        // device error bits (ERR_*) of earlier runs, kept until a host sync point reads them
     CTRL_M = 10,         // number of BVH leaves
     CTRL_NCELLS = 11,    // number of dense cells (DenseBox)
     CTRL_WORK_PRE = 12,  // work counters of the persistent traversal kernels
@@ -47,12 +47,29 @@ enum : int {
     CTRL_KIND_FILL = 19,   // 3 words: fill counters of the per-kind leaf lists
     CTRL_KIND_WORK = 22,   // 3 words: work counters of the per-kind main kernels
     CTRL_WORK_END = 25,    // end of the per-phase counters (cleared before each phase)
+    CTRL_ABORT = 26,       // error bits of the current run (ERR_*): set, every later stage does nothing
+    CTRL_ALGO = 27,        // the algorithm the current run uses (DBSCAN_ALGO_FDBSCAN / _DENSEBOX)
+    CTRL_KEYBITS = 28,     // DenseBox: cell-key bits of the current run's grid
+    CTRL_EST_FRAC = 29,    // automatic choice: estimated dense-point share (float bits)
+    CTRL_EST_OCC = 30,     // automatic choice: estimated mean cell occupancy (float bits)
     CTRL_LO = 32,          // MAX_DIM words: order-preserving min per axis
     CTRL_HI = 40,          // MAX_DIM words: order-preserving max per axis
     CTRL_WORDS = 48
 };
 
 constexpr unsigned ERR_STACK = 2u;  // traversal/refit limits exceeded (cannot happen for valid trees)
+
+// Whether a stage of the current run goes ahead: not once the run is
+// aborted (CTRL_ABORT: non-finite input, a sort that gave up), and, for a
+// stage of one algorithm's chain (algo >= 0), only if the run chose that
+// algorithm. All threads of a launch read the same words (written by earlier
+// launches), so the decision is uniform.
+__device__ __forceinline__ bool stage_on(const uint32_t* ctrl, int algo)
+{
+    if (!ctrl) return true;
+    if (*(volatile const uint32_t*)(ctrl + CTRL_ABORT) != 0u) return false;
+    return algo < 0 || *(volatile const uint32_t*)(ctrl + CTRL_ALGO) == (uint32_t)algo;
+}
 
 struct GridParams {
     float lo[MAX_DIM];
@@ -77,8 +94,12 @@ struct EstBuffers {
 // are counted on every (n >> 22)-th point, scaled): how many lie in DenseBox
 // cells (grid g) of at least min_pts points, and the summed point counts of
 // their cells (the size-biased mean occupancy once divided by the samples)
-cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, const GridParams& g, int min_pts,
-                                   const EstBuffers& eb, cudaStream_t s);
+// The estimate then decides the algorithm on the device: DenseBox from a
+// dense share of auto_fraction or a mean occupancy of auto_occupancy up,
+// FDbscan otherwise (CTRL_ALGO, CTRL_EST_FRAC, CTRL_EST_OCC).
+cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, const GridParams* g, int min_pts,
+                                   float auto_fraction, float auto_occupancy, const EstBuffers& eb, uint32_t* ctrl,
+                                   cudaStream_t s);
 
 struct DenseBoxTemps {
     uint8_t* pdense;    // n: 0 not dense, 1 dense cell within a tile, 2 dense cell as its own leaf
@@ -135,25 +156,37 @@ __device__ __forceinline__ uint64_t interleave(const uint32_t* c)
 }
 
 void launch_bounds(const float* pts, int64_t n, int dim, uint32_t* ctrl, cudaStream_t s);
+// the run's first kernel: moves CTRL_ABORT's bits into CTRL_ERR (kept for
+// the next host sync point), clears CTRL_ABORT and sets CTRL_ALGO
+void launch_run_begin(uint32_t* ctrl, int algo, cudaStream_t s);
+// DenseBox grid from the device-side bounds: cell side f * eps / sqrt(dim)
+// (Sec. 4.2), coarsened until every axis fits max_axis_bits; writes *gp and
+// CTRL_KEYBITS
+void launch_grid(uint32_t* ctrl, int dim, float eps, float factor, int max_axis_bits, GridParams* gp,
+                 cudaStream_t s);
+// FDbscan keys (gated on CTRL_ALGO == FDBSCAN): 32-bit Morton codes in 2D/3D
 void launch_morton32(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint32_t* keys,
                      uint32_t* vals, cudaStream_t s);
 // FDbscan keys above 3D: 64-bit Morton codes, `bits` per axis
 void launch_morton64(const float* pts, int64_t n, int dim, const uint32_t* ctrl, int bits, uint64_t* keys,
                      uint32_t* vals, cudaStream_t s);
-void launch_cellkey(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* keys, uint32_t* vals,
-                    cudaStream_t s);
 void launch_morton_generic(const float* pts, int64_t n, int dim, const GridParams& gp, uint64_t* out,
                            cudaStream_t s);
-void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, cudaStream_t s);
-// DenseBox keys packed above the point index for a keys-only sort, and the
-// gather that splits the sorted words into permutation and keys
-void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParams& gp, int idx_bits,
-                           uint64_t* words, cudaStream_t s);
+// FDbscan gather (gated): sorted points from the sort's permutation
+void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, void* sp, const uint32_t* ctrl,
+                   int algo, cudaStream_t s);
+// DenseBox keys packed above the point index for a keys-only sort (gated on
+// DENSEBOX), written to words0 or words1 as sort_dev_input_alt(host_passes,
+// the passes CTRL_KEYBITS needs) says; and the gather that splits the sorted
+// words into permutation and keys
+void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParams* gp, const uint32_t* ctrl,
+                           int idx_bits, int host_passes, uint64_t* words0, uint64_t* words1, cudaStream_t s);
 void launch_gather_packed(const float* pts, const uint64_t* words, int64_t n, int dim, int idx_bits, void* sp,
-                          uint32_t* perm, uint64_t* keys, cudaStream_t s);
+                          uint32_t* perm, uint64_t* keys, const uint32_t* ctrl, cudaStream_t s);
 cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t n, int dim, int min_pts, float e2,
                                    const DenseBoxTemps& t, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
                                    cudaStream_t s);
+// FDbscan leaves (gated on FDBSCAN): radix tiles of the Morton-sorted points
 cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBoxTemps& t, int2* leafr,
                                uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
 cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBoxTemps& t, int2* leafr,

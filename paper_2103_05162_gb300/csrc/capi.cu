@@ -158,6 +158,7 @@ struct Plan {
     int32_t* nlist;  // n * lcap neighbour indices (preprocessing lists)
     int32_t* ncount; // n neighbour counts capped at the largest minPts (multi-minPts runs)
     EstBuffers est;  // density estimate (automatic algorithm choice)
+    GridParams* grid; // DenseBox grid, computed on the device from the bounds
 };
 
 int64_t leaf_cap(int64_t n, int algo)
@@ -228,6 +229,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.est.slot = c.take<int32_t>(EST_SAMPLES);
     p.est.counts = c.take<uint32_t>(EST_SLOTS);
     p.est.result = c.take<uint32_t>(4);
+    p.grid = c.take<GridParams>(1);
     return c.off + 256;
 }
 
@@ -350,32 +352,23 @@ dbscan_status check_run_args(const void* points, int64_t n, int dim, float eps, 
     return DBSCAN_OK;
 }
 
-// DenseBox grid: cell side f * eps / sqrt(dim) (Sec. 4.2), coarsened when the
-// cell count per axis would exceed the key width (the per-cell guard keeps
-// the result exact for any cell size).
-GridParams densebox_grid(const float* lo, const float* hi, int dim, float eps, float factor, int* key_bits)
+// Bits per axis of the DenseBox cell keys: the Morton width of 64-bit keys
+// (21 in 3D, 31 in 2D, 63 / dim above), and no more than what leaves room for
+// the point index beside the key in one word, so that the keys-only sort of
+// packed words always applies (the grid is coarsened on the device to fit;
+// the per-cell guard keeps the result exact for any cell size).
+int densebox_axis_bits(int dim, int idx_bits)
 {
-    GridParams g{};
-    double h = (double)factor * (double)eps / std::sqrt((double)dim);
-    const int maxbits = dim == 3 ? 21 : (dim == 2 ? 31 : 63 / dim);  // 64-bit keys
-    const double maxcells = std::ldexp(1.0, maxbits);
-    double ext_max = 0.0;
-    for (int k = 0; k < dim; ++k) ext_max = std::fmax(ext_max, (double)hi[k] - (double)lo[k]);
-    if (ext_max / h >= maxcells - 2.0) h = ext_max / (maxcells - 2.0);
-    const float inv_h = (float)(1.0 / h);
-    int bits = 1;
-    for (int k = 0; k < dim; ++k) {
-        g.lo[k] = lo[k];
-        double c = std::floor(((double)hi[k] - (double)lo[k]) * (double)inv_h) + 1.0;
-        if (c > maxcells - 1.0) c = maxcells - 1.0;
-        g.cmax[k] = (uint32_t)c;  // one spare cell for rounding at the top
-        while (bits < maxbits && (std::ldexp(1.0, bits) - 1.0) < (double)g.cmax[k]) ++bits;
-    }
-    g.inv_h = inv_h;
-    g.bits = bits;
-    g.morton = 1;
-    *key_bits = bits * dim;
-    return g;
+    const int morton = dim == 3 ? 21 : (dim == 2 ? 31 : 63 / dim);
+    const int fit = (64 - idx_bits) / dim;
+    return morton < fit ? morton : fit;
+}
+
+int index_bits(int64_t n)
+{
+    int b = 1;
+    while (b < 32 && ((int64_t)1 << b) < n) ++b;
+    return b;
 }
 
 // ---------------------------------------------------------------------------
@@ -383,57 +376,36 @@ GridParams densebox_grid(const float* lo, const float* hi, int dim, float eps, f
 // ---------------------------------------------------------------------------
 enum Stage { ST_BOUNDS, ST_KEYS, ST_SORT, ST_GATHER, ST_LEAVES, ST_LBVH, ST_INIT, ST_PRE, ST_MAIN, ST_FINAL };
 
-// Stages a1-a7: bounds (one host wait for them), keys, sort, gather, leaves
-// (DenseBox cells dense for minPts = dense_mp), BVH. Fills the plan-dependent
-// fields of `a`.
+// Stages a1-a7: bounds, keys, sort, gather, leaves (DenseBox cells dense for
+// minPts = dense_mp), BVH. Fills the plan-dependent fields of `a`. Nothing
+// here waits for the device: the DenseBox grid is computed from the bounds
+// on the device (k_grid), the sort takes the passes the keys need there, and
+// the automatic choice (DBSCAN_ALGO_AUTO) enqueues both algorithms' key,
+// sort, gather and leaf stages, of which only the chosen chain runs
+// (CTRL_ALGO). A non-finite coordinate or a sort that gives up sets
+// CTRL_ABORT and every later stage does nothing; the next host sync point
+// (dbscan_stream_status, dbscan_run_host, dbscan_run_sync) reports it.
 dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const float* points, int64_t n, int dim,
                           float eps, int dense_mp, int algo, ClusterArgs& a, cudaStream_t s)
 {
-    w->last_algo = algo;
-    w->last_dense_fraction = -1.0f;
-    w->last_occupancy = -1.0f;
+    w->last_algo = algo == DBSCAN_ALGO_AUTO ? -2 : algo;  // -2: chosen on the device
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_LO, 0xff, MAX_DIM * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_HI, 0, MAX_DIM * sizeof(uint32_t), s));
-    TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_NONFINITE, 0, sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_M, 0, 2 * sizeof(uint32_t), s));
+    launch_run_begin(p.ctrl, algo, s);
     T.begin(ST_BOUNDS);
     launch_bounds(points, n, dim, p.ctrl, s);
     T.end();
     TRY_CUDA(cudaGetLastError());
-    TRY_CUDA(cudaMemcpyAsync(w->ctrl_host, p.ctrl, CTRL_WORDS * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    TRY_CUDA(cudaStreamSynchronize(s));
-    const uint32_t* hc = w->ctrl_host;
-    if (hc[CTRL_ERR] != 0) {
-        TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_ERR, 0, sizeof(uint32_t), s));
-        return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "earlier work on this stream reported device error bits 0x%x",
-                         hc[CTRL_ERR]);
-    }
-    if (hc[CTRL_NONFINITE] != 0) return set_error(DBSCAN_ERR_NONFINITE, "input coordinates contain NaN or Inf");
-    float lo[MAX_DIM] = {}, hi[MAX_DIM] = {};
-    for (int k = 0; k < dim; ++k) {
-        lo[k] = ord2f(hc[CTRL_LO + k]);
-        hi[k] = ord2f(hc[CTRL_HI + k]);
-    }
     const float e2 = eps * eps;
-
-    if (algo == DBSCAN_ALGO_AUTO) {
-        // the share of points in dense cells, from samples (one more host wait)
-        int key_bits = 0;
-        const GridParams g = densebox_grid(lo, hi, dim, eps, g_tuning.cell_factor, &key_bits);
-        TRY_CUDA(launch_density_estimate(points, n, dim, g, dense_mp, p.est, s));
-        TRY_CUDA(cudaMemcpyAsync(w->ctrl_host, p.est.result, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        TRY_CUDA(cudaStreamSynchronize(s));
-        const uint32_t dense_samples = w->ctrl_host[0];
-        const uint64_t occ_sum = (uint64_t)w->ctrl_host[2] | ((uint64_t)w->ctrl_host[3] << 32);
-        const int samples = n < EST_SAMPLES ? (int)n : EST_SAMPLES;
-        const float frac = (float)dense_samples / (float)samples;
-        const float occ = (float)((double)occ_sum / (double)samples);
-        algo = (frac >= g_tuning.auto_fraction[dim] || occ >= g_tuning.auto_occupancy[dim]) ? DBSCAN_ALGO_DENSEBOX
-                                                                                          : DBSCAN_ALGO_FDBSCAN;
-        w->last_algo = algo;
-        w->last_dense_fraction = frac;
-        w->last_occupancy = occ;
-    }
+    const bool fd = algo != DBSCAN_ALGO_DENSEBOX, db = algo != DBSCAN_ALGO_FDBSCAN;
+    const int idx_bits = index_bits(n);
+    const int db_axis_bits = densebox_axis_bits(dim, idx_bits);
+    const int db_key_bits = db_axis_bits * dim;
+    if (db) launch_grid(p.ctrl, dim, eps, g_tuning.cell_factor, db_axis_bits, p.grid, s);
+    if (algo == DBSCAN_ALGO_AUTO)
+        TRY_CUDA(launch_density_estimate(points, n, dim, p.grid, dense_mp, g_tuning.auto_fraction[dim],
+                                         g_tuning.auto_occupancy[dim], p.est, p.ctrl, s));
 
     SortBuffers sb;
     sb.keys_alt = p.keys_alt;
@@ -441,84 +413,75 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     sb.hist = p.hist;
     sb.status = p.status;
     sb.counters = p.counters;
-    sb.err = p.ctrl + CTRL_ERR;
+    sb.err = p.ctrl + CTRL_ABORT;  // a wait that runs out stops every later stage
+    sb.ctl.abort = p.ctrl + CTRL_ABORT;
+    sb.ctl.gate = p.ctrl + CTRL_ALGO;
     bool in_alt = false;
     const int64_t m_cap = leaf_cap(n, algo);
-    const uint32_t* perm = nullptr;
+    uint32_t* perm = nullptr;
 
-    if (algo == DBSCAN_ALGO_FDBSCAN && dim > 3) {
-        // 64-bit Morton codes
+    if (fd) {  // FDbscan: Morton codes of the points (Sec. 4.1)
+        SortBuffers sf = sb;
+        sf.ctl.gate_val = DBSCAN_ALGO_FDBSCAN;
         const int bits = fdbscan_bits(dim);
-        uint64_t* k64 = static_cast<uint64_t*>(p.keys);
-        T.begin(ST_KEYS);
-        launch_morton64(points, n, dim, p.ctrl, bits, k64, p.vals, s);
-        T.end();
-        T.begin(ST_SORT);
-        TRY_CUDA(sort_pairs_u64(k64, p.vals, n, bits * dim, sb, s, &in_alt));
-        T.end();
-        const uint64_t* keys_sorted = in_alt ? static_cast<uint64_t*>(p.keys_alt) : k64;
-        perm = in_alt ? p.vals_alt : p.vals;
-        T.begin(ST_GATHER);
-        launch_gather(points, perm, n, dim, p.sp, s);
-        T.end();
-        T.begin(ST_LEAVES);
-        TRY_CUDA(launch_tile_leaves64(keys_sorted, n, p.db, p.leafr, p.lkey, p.ctrl, s));
-        T.end();
-    } else if (algo == DBSCAN_ALGO_FDBSCAN) {
-        const int bits = fdbscan_bits(dim);
-        uint32_t* k32 = static_cast<uint32_t*>(p.keys);
-        T.begin(ST_KEYS);
-        launch_morton32(points, n, dim, p.ctrl, bits, k32, p.vals, s);
-        T.end();
-        T.begin(ST_SORT);
-        TRY_CUDA(sort_pairs_u32(k32, p.vals, n, bits * dim, sb, s, &in_alt));
-        T.end();
-        const uint32_t* keys_sorted = in_alt ? static_cast<uint32_t*>(p.keys_alt) : k32;
-        perm = in_alt ? p.vals_alt : p.vals;
-        T.begin(ST_GATHER);
-        launch_gather(points, perm, n, dim, p.sp, s);
-        T.end();
-        T.begin(ST_LEAVES);
-        TRY_CUDA(launch_tile_leaves(keys_sorted, n, p.db, p.leafr, p.lkey, p.ctrl, s));
-        T.end();
-    } else {
-        int key_bits = 0;
-        GridParams g = densebox_grid(lo, hi, dim, eps, g_tuning.cell_factor, &key_bits);
-        uint64_t* k64 = static_cast<uint64_t*>(p.keys);
-        uint64_t* k64_alt = static_cast<uint64_t*>(p.keys_alt);
-        int idx_bits = 1;
-        while (idx_bits < 32 && ((int64_t)1 << idx_bits) < n) ++idx_bits;
-        const uint64_t* keys_sorted;
-        if (key_bits + idx_bits <= 64) {
-            // cell key and point index in one word: a keys-only sort
+        if (dim > 3) {  // 64-bit Morton codes
+            uint64_t* k64 = static_cast<uint64_t*>(p.keys);
             T.begin(ST_KEYS);
-            launch_cellkey_packed(points, n, dim, g, idx_bits, k64, s);
+            launch_morton64(points, n, dim, p.ctrl, bits, k64, p.vals, s);
             T.end();
             T.begin(ST_SORT);
-            TRY_CUDA(sort_keys_u64(k64, n, idx_bits, key_bits, sb, s, &in_alt));
+            TRY_CUDA(sort_pairs_u64(k64, p.vals, n, bits * dim, sf, s, &in_alt));
             T.end();
-            uint64_t* unpacked = in_alt ? k64 : k64_alt;
-            perm = p.vals;
-            T.begin(ST_GATHER);
-            launch_gather_packed(points, in_alt ? k64_alt : k64, n, dim, idx_bits, p.sp, p.vals, unpacked, s);
-            T.end();
-            keys_sorted = unpacked;
-        } else {
-            T.begin(ST_KEYS);
-            launch_cellkey(points, n, dim, g, k64, p.vals, s);
-            T.end();
-            T.begin(ST_SORT);
-            TRY_CUDA(sort_pairs_u64(k64, p.vals, n, key_bits, sb, s, &in_alt));
-            T.end();
-            keys_sorted = in_alt ? k64_alt : k64;
+            const uint64_t* keys_sorted = in_alt ? static_cast<uint64_t*>(p.keys_alt) : k64;
             perm = in_alt ? p.vals_alt : p.vals;
             T.begin(ST_GATHER);
-            launch_gather(points, perm, n, dim, p.sp, s);
+            launch_gather(points, perm, n, dim, p.sp, p.ctrl, DBSCAN_ALGO_FDBSCAN, s);
+            T.end();
+            T.begin(ST_LEAVES);
+            TRY_CUDA(launch_tile_leaves64(keys_sorted, n, p.db, p.leafr, p.lkey, p.ctrl, s));
+            T.end();
+        } else {
+            uint32_t* k32 = static_cast<uint32_t*>(p.keys);
+            T.begin(ST_KEYS);
+            launch_morton32(points, n, dim, p.ctrl, bits, k32, p.vals, s);
+            T.end();
+            T.begin(ST_SORT);
+            TRY_CUDA(sort_pairs_u32(k32, p.vals, n, bits * dim, sf, s, &in_alt));
+            T.end();
+            const uint32_t* keys_sorted = in_alt ? static_cast<uint32_t*>(p.keys_alt) : k32;
+            perm = in_alt ? p.vals_alt : p.vals;
+            T.begin(ST_GATHER);
+            launch_gather(points, perm, n, dim, p.sp, p.ctrl, DBSCAN_ALGO_FDBSCAN, s);
+            T.end();
+            T.begin(ST_LEAVES);
+            TRY_CUDA(launch_tile_leaves(keys_sorted, n, p.db, p.leafr, p.lkey, p.ctrl, s));
             T.end();
         }
+    }
+    if (db) {  // DenseBox: grid-cell keys packed above the point index (Sec. 4.2)
+        SortBuffers sd = sb;
+        sd.ctl.gate_val = DBSCAN_ALGO_DENSEBOX;
+        sd.ctl.key_bits = p.ctrl + CTRL_KEYBITS;
+        uint64_t* k64 = static_cast<uint64_t*>(p.keys);
+        uint64_t* k64_alt = static_cast<uint64_t*>(p.keys_alt);
+        T.begin(ST_KEYS);
+        // (the sort runs no pass for n <= 1)
+        launch_cellkey_packed(points, n, dim, p.grid, p.ctrl, idx_bits, n > 1 ? sort_passes(db_key_bits) : 0, k64,
+                              k64_alt, s);
+        T.end();
+        T.begin(ST_SORT);
+        TRY_CUDA(sort_keys_u64(k64, n, idx_bits, db_key_bits, sd, s, &in_alt));
+        T.end();
+        // the permutation goes where FDbscan's would (one buffer for the
+        // stages after, whichever chain ran)
+        uint32_t* dperm = fd ? perm : p.vals;
+        uint64_t* unpacked = in_alt ? k64 : k64_alt;
+        T.begin(ST_GATHER);
+        launch_gather_packed(points, in_alt ? k64_alt : k64, n, dim, idx_bits, p.sp, dperm, unpacked, p.ctrl, s);
+        T.end();
+        perm = dperm;
         T.begin(ST_LEAVES);
-        TRY_CUDA(
-            launch_densebox_leaves(keys_sorted, p.sp, n, dim, dense_mp, e2, p.db, p.leafr, p.lkey, p.ctrl, s));
+        TRY_CUDA(launch_densebox_leaves(unpacked, p.sp, n, dim, dense_mp, e2, p.db, p.leafr, p.lkey, p.ctrl, s));
         T.end();
     }
     TRY_CUDA(cudaGetLastError());
@@ -540,8 +503,9 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     a.lcount = p.lcount;
     a.parent = p.parent;
     a.nmeta = p.nmeta;
-    a.pdense = algo == DBSCAN_ALGO_DENSEBOX ? p.db.pdense : nullptr;
-    a.dstart = algo == DBSCAN_ALGO_DENSEBOX ? p.db.dstart : nullptr;
+    // (automatic choice: the DenseBox flags are all zero when FDbscan ran)
+    a.pdense = db ? p.db.pdense : nullptr;
+    a.dstart = db ? p.db.dstart : nullptr;
     a.perm = perm;
     a.labels = p.labels;
     a.core = p.core;
@@ -704,14 +668,17 @@ dbscan_status workspace_status(Workspace* w, cudaStream_t s)
 {
     TRY_CUDA(cudaStreamSynchronize(s));
     if (!w || !w->main.base) return DBSCAN_OK;
-    uint32_t err = 0;
     Plan p;
     carve_plan(p, w->main.base, 0, 3, DBSCAN_ALGO_FDBSCAN, 0);
-    TRY_CUDA(cudaMemcpyAsync(&err, p.ctrl + CTRL_ERR, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    // the error bits of earlier runs (CTRL_ERR) and of the last one (CTRL_ABORT)
+    TRY_CUDA(cudaMemcpyAsync(w->ctrl_host, p.ctrl, CTRL_WORDS * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     TRY_CUDA(cudaStreamSynchronize(s));
+    const uint32_t err = w->ctrl_host[CTRL_ERR] | w->ctrl_host[CTRL_ABORT];
     if (err) {
         TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_ERR, 0, sizeof(uint32_t), s));
+        TRY_CUDA(cudaMemsetAsync(p.ctrl + CTRL_ABORT, 0, sizeof(uint32_t), s));
         TRY_CUDA(cudaStreamSynchronize(s));
+        if (err & ERR_NONFINITE) return set_error(DBSCAN_ERR_NONFINITE, "input coordinates contain NaN or Inf");
         return set_error(DBSCAN_ERR_DEVICE_TIMEOUT, "device error bits 0x%x", err);
     }
     return DBSCAN_OK;
@@ -732,6 +699,15 @@ dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
     return run_pipeline(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+}
+
+dbscan_status dbscan_run_sync(const float* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
+                              int32_t* labels_out, uint8_t* core_out, dbscan_stream stream)
+{
+    dbscan_status st = dbscan_run(points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, stream);
+    if (st != DBSCAN_OK || n == 0) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return workspace_status(get_workspace(s), s);
 }
 
 dbscan_status dbscan_run_multi(const float* points, int64_t n, int dim, float eps, const int32_t* min_pts,
@@ -795,8 +771,7 @@ dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, floa
     if (st != DBSCAN_OK) return st;
     TRY_CUDA(cudaMemcpyAsync(labels_host, dlab, lbytes, cudaMemcpyDeviceToHost, s));
     if (core_host) TRY_CUDA(cudaMemcpyAsync(core_host, dcore, (size_t)n, cudaMemcpyDeviceToHost, s));
-    TRY_CUDA(cudaStreamSynchronize(s));
-    return DBSCAN_OK;
+    return workspace_status(w, s);  // waits for the copies, then reports the run's device errors
 }
 
 dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, const int32_t* dims, const float* eps,
@@ -915,10 +890,28 @@ dbscan_status dbscan_last_choice(dbscan_stream stream, int* algo_out, float* est
 {
     t_err.clear();
     if (!algo_out || !estimates_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null argument");
-    Workspace* w = get_workspace(static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
     *algo_out = w ? w->last_algo : -1;
-    estimates_out[0] = w ? w->last_dense_fraction : -1.0f;
-    estimates_out[1] = w ? w->last_occupancy : -1.0f;
+    estimates_out[0] = -1.0f;
+    estimates_out[1] = -1.0f;
+    if (w && w->last_algo == -2 && w->main.base) {  // chosen on the device: wait and read it
+        TRY_CUDA(cudaStreamSynchronize(s));
+        TRY_CUDA(cudaMemcpyAsync(w->ctrl_host, w->main.base, CTRL_WORDS * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                 s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        const uint32_t a = w->ctrl_host[CTRL_ALGO];
+        *algo_out = (a == DBSCAN_ALGO_FDBSCAN || a == DBSCAN_ALGO_DENSEBOX) ? (int)a : -1;
+        memcpy(&estimates_out[0], &w->ctrl_host[CTRL_EST_FRAC], sizeof(float));
+        memcpy(&estimates_out[1], &w->ctrl_host[CTRL_EST_OCC], sizeof(float));
+    }
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_test_sort_hooks(int64_t wait_limit, int stall_first_tile)
+{
+    t_err.clear();
+    sort_set_test_hooks(wait_limit, stall_first_tile);
     return DBSCAN_OK;
 }
 

@@ -28,11 +28,9 @@ struct Workspace {
     // it from and join it back to the caller's stream
     cudaStream_t gstream = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-    // the algorithm the last run on this stream used, and the dense-point
-    // estimate behind it (-1 when the caller chose the algorithm)
+    // the algorithm the last run on this stream used (-1 before any; -2:
+    // chosen on the device, read from the control block on request)
     int last_algo = -1;
-    float last_dense_fraction = -1.0f;
-    float last_occupancy = -1.0f;
 };
 
 struct Tuning {

@@ -13,11 +13,12 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int TILE = 32;  // points per non-dense BVH leaf (one warp lane per point)
 constexpr int SORT_TILE_KEYS = 256 * 16;  // keys per look-back tile of the radix sort (256 threads x 16)
 
-// bits of the device error word
-constexpr unsigned ERR_SORT_TIMEOUT = 1u;
+// bits of the device error words
+constexpr unsigned ERR_SORT_TIMEOUT = 1u;  // a radix-sort look-back wait ran out
+constexpr unsigned ERR_NONFINITE = 4u;     // the input holds a NaN or an infinity
 
 // Upper bound on the iterations of any device-side wait. A wait that runs out
-// sets an error bit and proceeds, so no kernel can hang.
+// sets an error bit and gives up its step, so no kernel can hang.
 constexpr int SPIN_LIMIT = 1 << 22;
 
 // ---------------------------------------------------------------------------
@@ -523,14 +524,45 @@ int64_t launches_so_far();
 // ---------------------------------------------------------------------------
 
 // sort.cu
+// passes of an LSD radix sort over `bits` key bits (8-bit digits)
+__host__ __device__ __forceinline__ int sort_passes(int bits) { return (bits + 7) / 8; }
+
+// Device-side control of a sort inside the pipeline (all null: a plain sort).
+//  * gate / gate_val: the sort runs only if *gate == gate_val (the algorithm
+//    the run chose on the device);
+//  * abort: the sort does not run if *abort is nonzero when a pass starts;
+//  * key_bits: the key bits actually used, known on the device only, at most
+//    the `bits` the host launched for: passes beyond them do nothing, and the
+//    keys are written to the buffer (sort_dev_input_alt) from which the
+//    passes that do run leave the result where all `bits` would have.
+struct SortCtl {
+    const uint32_t* gate = nullptr;
+    uint32_t gate_val = 0;
+    const uint32_t* abort = nullptr;
+    const uint32_t* key_bits = nullptr;
+};
+// with host_passes launched and dev_passes needed: does the input go to the
+// alternate buffer?
+__host__ __device__ __forceinline__ bool sort_dev_input_alt(int host_passes, int dev_passes)
+{
+    return ((host_passes - dev_passes) & 1) != 0;
+}
+
 struct SortBuffers {
     void* keys_alt;        // n keys
     uint32_t* vals_alt;    // n values
     uint32_t* hist;        // 8 * 256
     uint32_t* status;      // passes * tiles * 256
     uint32_t* counters;    // 8
-    uint32_t* err;         // device error word
+    uint32_t* err;         // device error word (ERR_SORT_TIMEOUT)
+    SortCtl ctl;           // device-side control (pipeline sorts only)
 };
+// Test hooks of the look-back wait: the wait limit of every later sort
+// (spins; negative restores SPIN_LIMIT) and, if stall_first_tile, tile 0 of
+// every pass withholding its status words, so that every later tile's wait
+// on it runs out (the sort then reports ERR_SORT_TIMEOUT and writes nothing
+// from those tiles).
+void sort_set_test_hooks(int64_t wait_limit, int stall_first_tile);
 int64_t sort_tiles(int64_t n, int key_bytes);
 size_t sort_status_words(int64_t n, int key_bytes, int bits);
 // Sorts (keys, vals) by the low `bits` bits. On return *in_alt tells whether

@@ -6,14 +6,19 @@
 //
 // Forward progress: tiles take their index from an atomic counter when they
 // start, so a tile only ever waits for tiles that are already running. Every
-// wait is bounded (SPIN_LIMIT); a wait that runs out sets ERR_SORT_TIMEOUT in
-// the device error word instead of hanging.
+// wait is bounded (SPIN_LIMIT spins, or the test hook's limit); a tile whose
+// wait runs out sets ERR_SORT_TIMEOUT in the device error word, publishes no
+// prefix and scatters nothing (its output slots keep what they held), so a
+// timed-out sort never writes outside its buffers; later stages of the
+// pipeline read the error word and stop.
 //
 // This orders Morton codes / grid-cell keys (the space-filling-curve order of
 // Sec. 4.1 and the cell grouping of Sec. 4.2). A keys-only form sorts 64-bit
 // words that carry the key above the point's index (key << b | index) on
 // bits [b, b + key bits): a third less traffic per pass than separate
 // 64-bit keys and 32-bit values, in the same stable order.
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace gbd {
@@ -30,19 +35,42 @@ constexpr uint32_t FLAG_AGG = 1u << 30;
 constexpr uint32_t FLAG_PRE = 2u << 30;
 constexpr uint32_t VAL_MASK = (1u << 30) - 1;
 
+// The passes a launch of the sort takes part in, decided once per block (a
+// word another block sets during the launch must not split the block):
+// 0 if the sort is gated off or aborted, else the passes the keys need.
+__device__ __forceinline__ int sort_block_passes(const SortCtl& c, int host_passes, int* s_dec)
+{
+    if (threadIdx.x == 0) {
+        int p = host_passes;
+        if (c.gate && ld_relaxed(c.gate) != c.gate_val) p = 0;
+        if (c.abort && ld_relaxed(c.abort) != 0) p = 0;
+        if (p && c.key_bits) {
+            const int d = sort_passes((int)ld_relaxed(c.key_bits));
+            p = d < 1 ? 1 : (d < host_passes ? d : host_passes);
+        }
+        *s_dec = p;
+    }
+    __syncthreads();
+    return *s_dec;
+}
+
 template <typename K>
-__global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, int64_t n, int shift0, int passes,
-                                                  uint32_t* __restrict__ hist)
+__global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ k0, const K* __restrict__ k1, int64_t n,
+                                                  int shift0, int passes, SortCtl ctl, uint32_t* __restrict__ hist)
 {
     __shared__ uint32_t sh[8 * RADIX];
-    for (int i = threadIdx.x; i < passes * RADIX; i += THREADS) sh[i] = 0;
+    __shared__ int s_dec;
+    const int pd = sort_block_passes(ctl, passes, &s_dec);
+    if (pd == 0) return;
+    const K* __restrict__ keys = sort_dev_input_alt(passes, pd) ? k1 : k0;
+    for (int i = threadIdx.x; i < pd * RADIX; i += THREADS) sh[i] = 0;
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS) {
         K k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + 8 * p)) & 255u)], 1u);
+        for (int p = 0; p < pd; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + 8 * p)) & 255u)], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * RADIX; i += THREADS) {
+    for (int i = threadIdx.x; i < pd * RADIX; i += THREADS) {
         uint32_t v = sh[i];
         if (v) atomicAdd(&hist[i], v);
     }
@@ -79,12 +107,15 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
 // (three blocks per SM with values: the compiler then keeps every key, value
 // and rank in 80 registers without spilling, instead of taking 128 and
 // fitting two; four for keys only)
+//
+// Pass `pass` of `passes`: reads buffer 0 and writes buffer 1 on even passes
+// (the reverse on odd ones), or, under device control, as the passes the keys
+// need decide (sort_dev_input_alt); passes beyond those do nothing.
 template <typename K, bool VALS>
-__global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                      K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
-                                                      int shift, const uint32_t* __restrict__ hist,
-                                                      uint32_t* __restrict__ status, uint32_t* tile_counter,
-                                                      uint32_t* err)
+__global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
+    k_onesweep(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int shift0, int pass, int passes, SortCtl ctl,
+               const uint32_t* __restrict__ hist, uint32_t* __restrict__ status, uint32_t* tile_counter,
+               uint32_t* err, int wait_limit, int stall_first_tile)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     K* keys_s = reinterpret_cast<K*>(smem);
@@ -94,6 +125,16 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __r
     __shared__ uint32_t s_excl[RADIX];
     __shared__ uint32_t s_gofs[RADIX];
     __shared__ uint32_t s_warp[WARPS];
+    __shared__ int s_dec;
+
+    const int pd = sort_block_passes(ctl, passes, &s_dec);
+    if (pass >= pd) return;
+    const int sel = (sort_dev_input_alt(passes, pd) ? 1 : 0) ^ (pass & 1);
+    const K* __restrict__ kin = sel ? k1 : k0;
+    const uint32_t* __restrict__ vin = sel ? v1 : v0;
+    K* __restrict__ kout = sel ? k0 : k1;
+    uint32_t* __restrict__ vout = sel ? v0 : v1;
+    const int shift = shift0 + 8 * pass;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
@@ -147,13 +188,15 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __r
         total += c;
     }
     uint32_t* st = status + (size_t)tile * RADIX + tid;
-    st_relaxed(st, (tile == 0 ? FLAG_PRE : FLAG_AGG) | total);
+    const bool withhold = stall_first_tile && tile == 0;  // test hook: nothing published
+    if (!withhold) st_relaxed(st, (tile == 0 ? FLAG_PRE : FLAG_AGG) | total);
 
     const uint32_t excl = block_excl_scan(total, s_warp);
     s_excl[tid] = excl;
     const uint32_t dbase = block_excl_scan(hist[tid], s_warp);
 
     uint32_t prefix = 0;
+    bool gave_up = false;
     if (tile > 0) {
         int64_t j = (int64_t)tile - 1;
         int spins = 0;
@@ -161,8 +204,9 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __r
             const uint32_t s = ld_relaxed(status + (size_t)j * RADIX + tid);
             const uint32_t flag = s & ~VAL_MASK;
             if (flag == 0u) {
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > wait_limit) {
                     atomicOr(err, ERR_SORT_TIMEOUT);
+                    gave_up = true;
                     break;
                 }
                 __nanosleep(32);
@@ -172,10 +216,14 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __r
             if (flag == FLAG_PRE) break;
             --j;
         }
-        st_relaxed(st, FLAG_PRE | ((prefix + total) & VAL_MASK));
+        // a digit whose wait ran out publishes no prefix: later tiles look
+        // past it to the aggregates before it (or run out themselves)
+        if (!gave_up) st_relaxed(st, FLAG_PRE | ((prefix + total) & VAL_MASK));
     }
     s_gofs[tid] = dbase + prefix;
-    __syncthreads();
+    // any digit without its offset: the tile's positions are unknown, so it
+    // writes nothing
+    if (__syncthreads_or(gave_up)) return;
 
     // tile-local positions (sorted by digit, stable), then stage in shared memory
 #pragma unroll
@@ -203,22 +251,34 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4) k_onesweep(const K* __r
     }
 }
 
-// sorts by bits [shift0, shift0 + bits) of the keys; vals null: keys only
+std::atomic<int> g_wait_limit{SPIN_LIMIT};
+std::atomic<int> g_stall_first_tile{0};
+
+// sorts by bits [shift0, shift0 + bits) of the keys; vals null: keys only.
+// Under device control (sb.ctl.key_bits) `bits` is an upper bound and the
+// keys must have been written to the buffer sort_dev_input_alt names; the
+// result lands where `bits` would leave it either way (*in_alt).
 template <typename K>
 cudaError_t sort_pairs(K* keys, uint32_t* vals, int64_t n, int shift0, int bits, const SortBuffers& sb,
                        cudaStream_t s, bool* in_alt)
 {
     *in_alt = false;
     if (n <= 1 || bits <= 0) return cudaSuccess;
-    const int passes = (bits + 7) / 8;
+    const int passes = sort_passes(bits);
     const int64_t tiles = (n + TILE_ITEMS - 1) / TILE_ITEMS;
     cudaError_t e;
     if ((e = cudaMemsetAsync(sb.hist, 0, sizeof(uint32_t) * RADIX * passes, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sb.counters, 0, sizeof(uint32_t) * passes, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sb.status, 0, sizeof(uint32_t) * RADIX * (size_t)tiles * passes, s)) != cudaSuccess)
         return e;
+    K* k_alt = static_cast<K*>(sb.keys_alt);
+    // once a wait has run out, no later pass may run: its input holds slots
+    // the timed-out tiles never wrote, and ranks computed from them could
+    // point past the end of the output
+    SortCtl ctl = sb.ctl;
+    if (!ctl.abort) ctl.abort = sb.err;
     const int hist_blocks = (int)(tiles < 1216 ? tiles : 1216);
-    k_hist<K><<<hist_blocks, THREADS, 0, s>>>(keys, n, shift0, passes, sb.hist);
+    k_hist<K><<<hist_blocks, THREADS, 0, s>>>(keys, k_alt, n, shift0, passes, ctl, sb.hist);
     note_launches(1);
     const bool with_vals = vals != nullptr;
     const size_t smem = TILE_ITEMS * (sizeof(K) + (with_vals ? sizeof(uint32_t) : 0));
@@ -226,24 +286,18 @@ cudaError_t sort_pairs(K* keys, uint32_t* vals, int64_t n, int shift0, int bits,
     if ((e = cudaFuncSetAttribute(with_vals ? k_onesweep<K, true> : k_onesweep<K, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    K* kin = keys;
-    uint32_t* vin = vals;
-    K* kout = static_cast<K*>(sb.keys_alt);
-    uint32_t* vout = sb.vals_alt;
+    const int limit = g_wait_limit.load(std::memory_order_relaxed);
+    const int stall = g_stall_first_tile.load(std::memory_order_relaxed);
     for (int p = 0; p < passes; ++p) {
         if (with_vals)
-            k_onesweep<K, true><<<(unsigned)tiles, THREADS, smem, s>>>(kin, vin, kout, vout, n, shift0 + 8 * p,
-                                                                       sb.hist + RADIX * p,
-                                                                       sb.status + (size_t)RADIX * tiles * p,
-                                                                       sb.counters + p, sb.err);
+            k_onesweep<K, true><<<(unsigned)tiles, THREADS, smem, s>>>(
+                keys, vals, k_alt, sb.vals_alt, n, shift0, p, passes, ctl, sb.hist + RADIX * p,
+                sb.status + (size_t)RADIX * tiles * p, sb.counters + p, sb.err, limit, stall);
         else
-            k_onesweep<K, false><<<(unsigned)tiles, THREADS, smem, s>>>(kin, nullptr, kout, nullptr, n,
-                                                                        shift0 + 8 * p, sb.hist + RADIX * p,
-                                                                        sb.status + (size_t)RADIX * tiles * p,
-                                                                        sb.counters + p, sb.err);
+            k_onesweep<K, false><<<(unsigned)tiles, THREADS, smem, s>>>(
+                keys, nullptr, k_alt, nullptr, n, shift0, p, passes, ctl, sb.hist + RADIX * p,
+                sb.status + (size_t)RADIX * tiles * p, sb.counters + p, sb.err, limit, stall);
         note_launches(1);
-        K* tk = kin; kin = kout; kout = tk;
-        uint32_t* tv = vin; vin = vout; vout = tv;
     }
     *in_alt = (passes & 1) != 0;
     return cudaGetLastError();
@@ -259,8 +313,15 @@ int64_t sort_tiles(int64_t n, int key_bytes)
 
 size_t sort_status_words(int64_t n, int key_bytes, int bits)
 {
-    const int passes = (bits + 7) / 8;
+    const int passes = sort_passes(bits);
     return (size_t)RADIX * (size_t)sort_tiles(n, key_bytes) * (size_t)(passes > 0 ? passes : 1);
+}
+
+void sort_set_test_hooks(int64_t wait_limit, int stall_first_tile)
+{
+    g_wait_limit.store(wait_limit < 0 ? SPIN_LIMIT : (int)(wait_limit > SPIN_LIMIT ? SPIN_LIMIT : wait_limit),
+                       std::memory_order_relaxed);
+    g_stall_first_tile.store(stall_first_tile ? 1 : 0, std::memory_order_relaxed);
 }
 
 cudaError_t sort_pairs_u32(uint32_t* keys, uint32_t* vals, int64_t n, int bits, const SortBuffers& sb,

@@ -1421,8 +1421,10 @@ __global__ void k_init_from_counts(const uint8_t* __restrict__ pdense, const int
 // rest of it; points of dense cells are core in any case (every one of them
 // has at least minPts neighbours inside its cell).
 __global__ void k_core_from_input(const uint32_t* __restrict__ perm, const uint8_t* __restrict__ core_in,
-                                  const uint8_t* __restrict__ pdense, int64_t n, uint8_t* __restrict__ core)
+                                  const uint8_t* __restrict__ pdense, int64_t n, uint8_t* __restrict__ core,
+                                  const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;  // aborted run: perm may hold stale words
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         core[i] = ((pdense && pdense[i]) || core_in[perm[i]]) ? 1 : 0;
 }
@@ -1445,8 +1447,9 @@ __global__ void k_init(const uint8_t* __restrict__ pdense, const int32_t* __rest
 
 // full compression (Sec. 4.3) and the smallest input index per root
 __global__ void k_finalize(int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
-                           int64_t n, int32_t* __restrict__ canon)
+                           int64_t n, int32_t* __restrict__ canon, const uint32_t* __restrict__ ctrl)
 {
+    if (!stage_on(ctrl, -1)) return;
     // warp-uniform trip count: warp_atomic_min needs all 32 lanes
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
@@ -1460,8 +1463,12 @@ __global__ void k_finalize(int32_t* labels, const uint8_t* __restrict__ core, co
 // output in input order: canonical label of the cluster, or -1
 __global__ void k_relabel(const int32_t* labels, const uint8_t* __restrict__ core, const uint32_t* __restrict__ perm,
                           int64_t n, int mode, const int32_t* __restrict__ canon, int32_t* __restrict__ out,
-                          uint8_t* __restrict__ core_out)
+                          uint8_t* __restrict__ core_out, const uint32_t* __restrict__ ctrl)
 {
+    // aborted run (non-finite input, a sort that gave up): perm may hold
+    // stale words, so nothing is written; the error is reported at the next
+    // host sync point
+    if (!stage_on(ctrl, -1)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const bool c = core[i] != 0;
         const int r = uf_root(labels, (int)i);
@@ -1634,7 +1641,7 @@ cudaError_t launch_cluster_core_from_input(const ClusterArgs& a, const uint8_t* 
 {
     int64_t gn = (a.n + 255) / 256;
     if (gn > 152 * 16) gn = 152 * 16;
-    k_core_from_input<<<(unsigned)gn, 256, 0, s>>>(a.perm, core_in, a.pdense, a.n, a.core);
+    k_core_from_input<<<(unsigned)gn, 256, 0, s>>>(a.perm, core_in, a.pdense, a.n, a.core, a.ctrl);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1643,8 +1650,9 @@ cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint
 {
     int64_t gn = (a.n + 255) / 256;
     if (gn > 152 * 16) gn = 152 * 16;
-    k_finalize<<<(unsigned)gn, 256, 0, s>>>(a.labels, a.core, a.perm, a.n, a.canon);
-    k_relabel<<<(unsigned)gn, 256, 0, s>>>(a.labels, a.core, a.perm, a.n, a.mode, a.canon, labels_out, core_out);
+    k_finalize<<<(unsigned)gn, 256, 0, s>>>(a.labels, a.core, a.perm, a.n, a.canon, a.ctrl);
+    k_relabel<<<(unsigned)gn, 256, 0, s>>>(a.labels, a.core, a.perm, a.n, a.mode, a.canon, labels_out, core_out,
+                                           a.ctrl);
     note_launches(2);
     return cudaGetLastError();
 }

@@ -135,17 +135,30 @@ def test_wide_cell_keys(d):
         check(X, eps, mp, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX)
 
 
-@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("algo", ALGOS + [gb.ALGO_AUTO])
 def test_nonfinite_input_is_rejected(algo):
+    """A NaN or infinity is found on the device: dbscan_run returns at once,
+    writes no label, and the next sync point reports NONFINITE; the stream
+    then serves the next run normally."""
     X = blobs(1000, 3, 1)
     X[17, 2] = np.nan
     pts = torch.from_numpy(X).cuda()
+    labels = torch.full((1000,), -7, dtype=torch.int32, device="cuda")
+    gb.dbscan_run(pts, 0.05, 3, algo=algo, labels_out=labels)
     with pytest.raises(gb.DbscanError) as e:
-        gb.dbscan_run(pts, 0.05, 3, algo=algo)
+        gb.stream_status()
     assert e.value.name == "NONFINITE"
+    assert (labels.cpu().numpy() == -7).all()
     X[17, 2] = np.inf
-    with pytest.raises(gb.DbscanError):
-        gb.dbscan_run(torch.from_numpy(X).cuda(), 0.05, 3, algo=algo)
+    with pytest.raises(gb.DbscanError) as e:
+        gb.dbscan_run(torch.from_numpy(X).cuda(), 0.05, 3, algo=algo, sync=True)
+    assert e.value.name == "NONFINITE"
+    with pytest.raises(gb.DbscanError) as e:
+        gb.dbscan_run_host(X, 0.05, 3, algo=algo)
+    assert e.value.name == "NONFINITE"
+    gb.stream_status()  # cleared
+    X[17, 2] = 0.5
+    check(X, 0.05, 3, gb.MODE_DBSCAN, algo if algo != gb.ALGO_AUTO else gb.ALGO_DENSEBOX)
 
 
 # ------------------------------------------------------- medium, full oracle
@@ -317,3 +330,57 @@ def test_lbvh_topology_invariants():
             llo, lhi = (l - (m - 1),) * 2 if l >= m - 1 else tuple(rg[l])
             rlo, rhi = (r - (m - 1),) * 2 if r >= m - 1 else tuple(rg[r])
             assert llo == lo and rhi == hi and lhi + 1 == rlo
+
+
+# ---------------------------------------------------------------- boundary
+
+def test_dbscan_run_returns_before_the_device_finishes():
+    """dbscan_run only enqueues: right after it returns, an event recorded
+    behind its work is still pending on a 2^22-point input (about 2 ms of
+    device work), and the results match a synchronous run."""
+    n = 1 << 22
+    X = halos(n, 7, n_halos=12000)
+    eps = halo_eps(n)
+    pts = torch.from_numpy(X).cuda()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    for algo in (gb.ALGO_DENSEBOX, gb.ALGO_FDBSCAN, gb.ALGO_AUTO):
+        gb.dbscan_run(pts, eps, 10, algo=algo, labels_out=labels)  # sizes the workspace
+        torch.cuda.synchronize()
+        pending = 0
+        for _ in range(5):
+            gb.dbscan_run(pts, eps, 10, algo=algo, labels_out=labels)
+            ev = torch.cuda.Event()
+            ev.record()
+            pending += 0 if ev.query() else 1
+            torch.cuda.synchronize()
+        assert pending >= 4, f"algo {algo}: the call waited for the device ({pending} of 5 pending)"
+        gb.stream_status()
+        ref = gb.dbscan_run(pts, eps, 10, algo=algo, sync=True)
+        assert torch.equal(ref, labels)
+
+
+def test_sort_wait_that_runs_out_is_reported_and_the_next_sort_is_correct():
+    """The radix sort's bounded look-back wait, made to run out by a test
+    hook (the first tile of each pass publishes nothing, so every later
+    tile's wait on it ends at a short limit): the sort returns
+    DEVICE_TIMEOUT instead of hanging; with the hooks off the next sort is
+    exact and reports nothing."""
+    rs = np.random.default_rng(31)
+    n, bits = 1 << 20, 40
+    keys = rs.integers(0, 1 << bits, size=n, dtype=np.int64)
+    vals = np.arange(n, dtype=np.int32)
+    k = torch.from_numpy(keys.copy()).cuda()
+    v = torch.from_numpy(vals.copy()).cuda()
+    gb.test_sort_hooks(wait_limit=2000, stall_first_tile=True)
+    try:
+        with pytest.raises(gb.DbscanError) as e:
+            gb.sort_pairs_u64(k, v, bits)
+        assert e.value.name == "DEVICE_TIMEOUT"
+    finally:
+        gb.test_sort_hooks()
+    k = torch.from_numpy(keys.copy()).cuda()
+    v = torch.from_numpy(vals.copy()).cuda()
+    gb.sort_pairs_u64(k, v, bits)
+    order = np.argsort(keys, kind="stable")
+    assert (v.cpu().numpy() == order).all() and (k.cpu().numpy() == keys[order]).all()
+    gb.stream_status()
