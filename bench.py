@@ -223,6 +223,8 @@ def run_gb300(args, rank: int, world: int) -> None:
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     gb.load()
+    if args.border_lists is not None:
+        gb.set_border_lists(bool(args.border_lists))
     algo = gb.ALGO_DENSEBOX if args.algo == "densebox" else gb.ALGO_FDBSCAN
     X, eps = workload(args.n, args.seed + rank)
     n, d = X.shape
@@ -323,6 +325,7 @@ def run_gb300(args, rank: int, world: int) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(n, eps, args.min_pts), "n": n, "dim": d, "eps": eps,
                        "min_pts": args.min_pts, "algo": args.algo, "mode": "dbscan",
+                       "border_claims": "neighbour lists" if gb.border_lists() else "main traversal (no lists)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (201 MB of points; multi-GB working set per step)"},
             "roofline": roofline,
@@ -587,6 +590,9 @@ def main():
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--border-lists", type=int, choices=[0, 1], default=None,
+                    help="border claims from per-point neighbour lists (1) or in the main traversal (0); "
+                         "default: the library's default")
     ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep", "slabs"], default="step",
                     help="step: the headline line (default); batch: fused batch vs per-instance runs; "
                          "serve: Poisson-arrival serving vs sequential runs; sweep: several minPts over one "

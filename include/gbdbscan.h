@@ -243,6 +243,25 @@ const char* dbscan_last_error(void);
 dbscan_status dbscan_set_tuning(int block_size, float cell_factor);
 
 /*
+ * How border points join a cluster in DBSCAN mode (Sec. 3.2, Algorithm 3:
+ * a core point x within eps of a non-core point y claims y, CAS(labels[y], y,
+ * find(x))). Process-wide; set it before enqueueing work.
+ *   on = 0: the claims are made in the main traversal as core points find
+ *     their non-core neighbours; no per-point neighbour list is stored, so
+ *     the memory is O(n) whatever minPts (Sec. 3.2).
+ *   on = 1 (default): for 3 <= minPts <= 32, preprocessing keeps each
+ *     point's neighbours outside its tile in a list of minPts - 1 entries
+ *     (4 (minPts - 1) bytes per point: 604 MB for 2^24 points at minPts 10);
+ *     a point that ends non-core then claims its first core neighbour from
+ *     the list, and non-core points take no part in the main traversal.
+ * Both give a valid border label (one of its core neighbours' clusters) and
+ * identical core points, core labels and noise. dbscan_border_lists()
+ * returns the current setting.
+ */
+dbscan_status dbscan_set_border_lists(int on);
+int dbscan_border_lists(void);
+
+/*
  * Automatic algorithm choice (DBSCAN_ALGO_AUTO) for data of dimension dim
  * (2 to 8): DenseBox when the estimated share of points in dense cells is at
  * least dense_fraction (in [0, 1]) or the estimated mean cell occupancy is at

@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
             "dbscan_profile_collect": [vp, vp, vp],
             "dbscan_last_stats": [vp, vp],
             "dbscan_test_sort_hooks": [i64, i32],
+            "dbscan_set_border_lists": [i32],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -106,6 +107,8 @@ def load(build_if_missing: bool = True):
         lib.dbscan_last_error.restype = ctypes.c_char_p
         lib.dbscan_profile_stage_name.argtypes = [i32]
         lib.dbscan_profile_stage_name.restype = ctypes.c_char_p
+        lib.dbscan_border_lists.argtypes = []
+        lib.dbscan_border_lists.restype = i32
         lib.dbscan_kernel_launches.argtypes = []
         lib.dbscan_kernel_launches.restype = i64
         _lib = lib
@@ -400,7 +403,18 @@ def last_stats(stream=None) -> dict:
     return {"leaves": int(out[0]), "dense_cells": int(out[1])}
 
 
-def test_sort_hooks(wait_limit: int = -1, stall_first_tile: bool = False):
+def set_border_lists(on: bool):
+    """Border claims from preprocessing's per-point neighbour lists (True,
+    the default) or by core points in the main traversal with no per-point
+    list (False); see dbscan_set_border_lists."""
+    _check(load().dbscan_set_border_lists(1 if on else 0))
+
+
+def border_lists() -> bool:
+    return bool(load().dbscan_border_lists())
+
+
+def sort_test_hooks(wait_limit: int = -1, stall_first_tile: bool = False):
     """Test hooks of the radix sort's bounded wait (see dbscan_test_sort_hooks);
     (-1, False) restores the defaults."""
     _check(load().dbscan_test_sort_hooks(int(wait_limit), 1 if stall_first_tile else 0))

@@ -49,6 +49,7 @@ dbscan_status cuda_error(cudaError_t e, const char* what)
 // (above 3D the 3D thresholds: FDbscan's Morton grid is coarse there too)
 Tuning g_tuning = {128,
                    1.0f,
+                   1,
                    {0.0f, 0.0f, DEFAULT_AUTO_FRACTION_2D, DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D,
                     DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D,
                     DEFAULT_AUTO_FRACTION_3D},
@@ -932,6 +933,16 @@ dbscan_status dbscan_set_auto_threshold(int dim, float dense_fraction, float occ
     g_tuning.auto_occupancy[dim] = occupancy;
     return DBSCAN_OK;
 }
+
+dbscan_status dbscan_set_border_lists(int on)
+{
+    t_err.clear();
+    if (on != 0 && on != 1) return set_error(DBSCAN_ERR_INVALID_ARG, "on must be 0 or 1");
+    g_tuning.border_lists = on;
+    return DBSCAN_OK;
+}
+
+int dbscan_border_lists(void) { return g_tuning.border_lists; }
 
 dbscan_status dbscan_set_tuning(int block_size, float cell_factor)
 {

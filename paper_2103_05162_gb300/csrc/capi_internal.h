@@ -36,6 +36,10 @@ struct Workspace {
 struct Tuning {
     int block;             // traversal block size (threads)
     float cell_factor;     // DenseBox cell side factor f in (0, 1]
+    // border claims (DBSCAN mode): 1 = from preprocessing's per-point
+    // neighbour lists, 0 = by core points during the main traversal (no
+    // per-point list; Algorithm 3 as written)
+    int border_lists;
     // DBSCAN_ALGO_AUTO, per dimension (index 2, 3): DenseBox from this
     // estimated dense-point share up, or from this estimated mean cell
     // occupancy up
@@ -60,14 +64,19 @@ Workspace* get_workspace(cudaStream_t s);
 cudaError_t ensure_arena(Arena& a, size_t bytes, cudaStream_t s);
 void free_workspace(Workspace* w);
 void release_stream_workspace(cudaStream_t s);
-// Neighbour lists of preprocessing (DBSCAN mode, 3 <= minPts <= 32): every
-// point keeps up to minPts - 1 of its neighbours outside its own tile, which
-// is all of them when it ends non-core; 0 means no lists.
+// Neighbour lists of preprocessing (DBSCAN mode, 3 <= minPts <= 32, border
+// lists switched on): every point keeps up to minPts - 1 of its neighbours
+// outside its own tile, which is all of them when it ends non-core; 0 means
+// no lists (core points then claim their border neighbours in the main phase).
 constexpr int LIST_MAX_MINPTS = 32;
 inline int list_cap(int min_pts, int mode)
 {
-    return (mode == DBSCAN_MODE_DBSCAN && min_pts > 2 && min_pts <= LIST_MAX_MINPTS) ? min_pts - 1 : 0;
+    return (g_tuning.border_lists && mode == DBSCAN_MODE_DBSCAN && min_pts > 2 && min_pts <= LIST_MAX_MINPTS)
+               ? min_pts - 1
+               : 0;
 }
+// the list capacity a batch of any minPts may need
+inline int list_cap_max() { return g_tuning.border_lists ? LIST_MAX_MINPTS - 1 : 0; }
 size_t workspace_bytes(int64_t n, int dim, int algo, int min_pts, int mode);
 size_t workspace_bytes_multi(int64_t n, int dim, int algo, int max_min_pts, int mode);
 dbscan_status run_pipeline(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,

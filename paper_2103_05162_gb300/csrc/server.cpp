@@ -76,7 +76,7 @@ struct dbscan_server {
     {
         return pick_group(queue, group, used, budget, lim, [&](int64_t pts, int count) {
             // list capacity of the largest minPts a batch can have
-            return batch_workspace_bytes(pts, count, group[0]->algo, LIST_MAX_MINPTS - 1);
+            return batch_workspace_bytes(pts, count, group[0]->algo, list_cap_max());
         });
     }
 

@@ -2,7 +2,8 @@
 the workloads at the sizes the benchmark runs them.
 
 * 3D halos, 2^24 points (eps = 0.2 x mean spacing), minPts 10 and 2, both
-  modes, DenseBox and FDbscan;
+  modes, DenseBox and FDbscan, border claims from lists and in the main
+  traversal;
 * 2D roads, 4,194,304 points (eps 2e-4, minPts 10), both modes, both
   algorithms;
 * the 4096-instance batch (lognormal sizes, 164M points), one fused
@@ -89,6 +90,19 @@ def test_halos_16m_full_oracle(halos16m, mp, mode, algo):
     assert ref[1].any() and (ref[0] == -1).any()
     if mp == 10:
         assert (~ref[1] & (ref[0] >= 0)).any()
+
+
+def test_halos_16m_full_oracle_without_border_lists(halos16m):
+    """The benchmark workload with border claims made in the main traversal
+    (no per-point neighbour list), every point compared with the oracle."""
+    X, eps, refs = halos16m
+    ref, sets = refs[10]
+    gb.set_border_lists(False)
+    try:
+        lab, core = _gpu(X, eps, 10, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX)
+    finally:
+        gb.set_border_lists(True)
+    assert_matches_oracle(X, eps, 10, gb.MODE_DBSCAN, lab, core, ref=ref, sets=sets)
 
 
 # ------------------------------------------------------------ 2D roads, 4M

@@ -371,16 +371,45 @@ def test_sort_wait_that_runs_out_is_reported_and_the_next_sort_is_correct():
     vals = np.arange(n, dtype=np.int32)
     k = torch.from_numpy(keys.copy()).cuda()
     v = torch.from_numpy(vals.copy()).cuda()
-    gb.test_sort_hooks(wait_limit=2000, stall_first_tile=True)
+    gb.sort_test_hooks(wait_limit=2000, stall_first_tile=True)
     try:
         with pytest.raises(gb.DbscanError) as e:
             gb.sort_pairs_u64(k, v, bits)
         assert e.value.name == "DEVICE_TIMEOUT"
     finally:
-        gb.test_sort_hooks()
+        gb.sort_test_hooks()
     k = torch.from_numpy(keys.copy()).cuda()
     v = torch.from_numpy(vals.copy()).cuda()
     gb.sort_pairs_u64(k, v, bits)
     order = np.argsort(keys, kind="stable")
     assert (v.cpu().numpy() == order).all() and (k.cpu().numpy() == keys[order]).all()
     gb.stream_status()
+
+
+# ------------------------------------------------- border claims without lists
+
+@pytest.fixture
+def no_border_lists():
+    gb.set_border_lists(False)
+    try:
+        yield
+    finally:
+        gb.set_border_lists(True)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("mode", MODES)
+def test_claims_in_the_main_traversal_without_lists(no_border_lists, mode, algo):
+    """Border points claimed by core points during the main traversal, with
+    no per-point neighbour list (Algorithm 3 as written): blobs, halos,
+    roads and lattice ties against the oracle, for minPts from 3 to 40."""
+    assert not gb.border_lists()
+    check(blobs(16384, 3, 4), 0.03, 5, mode, algo)
+    n = 1 << 18
+    check(halos(n, 13, n_halos=800), halo_eps(n), 10, mode, algo)
+    X = roads(1 << 19, 5)
+    check(X, float(np.float32(2e-4 * (4194304 / (1 << 19)) ** 0.5)), 10, mode, algo)
+    rs = np.random.default_rng(8)
+    L = rs.integers(0, 12, size=(3000, 2)).astype(np.float32)
+    for mp in (3, 4, 9, 40):
+        check(L, 1.0, mp, mode, algo)
