@@ -411,67 +411,135 @@ __global__ void k_dense_classify(const uint64_t* __restrict__ keys, const typena
     }
 }
 
-// Common-prefix length of sorted keys i and j (-1 outside [0, n)), equal keys
-// told apart by index: the delta of Karras (2012).
+// Common-prefix length of the sorted keys a (at position pa) and b (at
+// position pb, -1 outside [0, n)), equal keys told apart by position: the
+// delta of Karras (2012).
 template <typename K>
-__device__ __forceinline__ int kdelta_t(const K* __restrict__ k, int64_t n, int64_t i, int64_t j)
+__device__ __forceinline__ int key_delta(K a, int64_t pa, K b, int64_t pb, int64_t n)
 {
-    if (j < 0 || j >= n) return -1;
-    const K a = k[i], b = k[j];
     constexpr int KB = 8 * (int)sizeof(K);
+    if (pb < 0 || pb >= n) return -1;
     if (a != b) return sizeof(K) == 8 ? __clzll((long long)(a ^ b)) : __clz((int)(a ^ b));
-    return KB + __clz((int)((uint32_t)i ^ (uint32_t)j));
+    return KB + __clz((int)((uint32_t)pa ^ (uint32_t)pb));
 }
 
-// Does the radix-tree node that splits points g and g+1 cover more than T
-// points? Its range is the run of keys sharing at least delta(g, g+1) leading
-// bits with key g; the run is found by binary search within T of g on each
-// side (reaching a window's end already means more than T).
 template <typename K>
-__device__ __forceinline__ bool radix_split_exceeds(const K* __restrict__ k, int64_t n, int64_t g, int T)
+__device__ __forceinline__ K shfl_key(K v, int src)
 {
-    const int d = kdelta_t(k, n, g, g + 1);
-    // delta(g, j) does not grow as j moves away from g, so single probes
-    // decide most splits: T - 1 points on one side of g already in the run
-    // means more than T in all; fewer than T/2 - 1 on each side means at
-    // most T - 2
-    if (kdelta_t(k, n, g, g - (T - 1)) >= d || kdelta_t(k, n, g, g + T) >= d) return true;
-    const int h = T / 2 - 1;
-    if (kdelta_t(k, n, g, g - h) < d && kdelta_t(k, n, g, g + 1 + h) < d) return false;
-    int64_t lo = g - T < 0 ? 0 : g - T, hi = g;  // smallest j in [lo, g] with delta(g, j) >= d
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (kdelta_t(k, n, g, mid) >= d) hi = mid; else lo = mid + 1;
+    if constexpr (sizeof(K) == 8) {
+        const uint32_t lo = __shfl_sync(FULL, (uint32_t)v, src), hi = __shfl_sync(FULL, (uint32_t)(v >> 32), src);
+        return (K)(((uint64_t)hi << 32) | lo);
+    } else {
+        return (K)__shfl_sync(FULL, (uint32_t)v, src);
     }
-    const int64_t a = lo;
-    lo = g + 1;
-    hi = g + 1 + T > n - 1 ? n - 1 : g + 1 + T;  // largest j in [g+1, hi] with delta(g, j) >= d
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (kdelta_t(k, n, g, mid) >= d) lo = mid; else hi = mid - 1;
-    }
-    const int64_t b = lo;
-    return (b - a + 1) > T;
 }
 
-// leaf starts: the first point of every dense cell larger than a tile;
-// elsewhere a new tile starts after such a cell and wherever the radix-tree
-// node splitting two neighbours covers more than T points. Tiles are then the maximal
-// subtrees of at most T points (spatially compact, unlike fixed runs of T in
-// Morton order, which can straddle a jump of the curve).
+// Leaf starts. A new leaf starts at point i where the node of the points'
+// radix tree (Karras: keys with position tie-break) that splits i - 1 from i
+// covers more than TILE points -- tiles are then the maximal subtrees of at
+// most TILE points, spatially compact unlike fixed runs in Morton order; and
+// at the first point of every dense cell larger than a tile, after such a
+// cell, and (batches) where the instance changes.
+// The node splitting g and g + 1 has prefix length d = delta(g, g + 1) and
+// covers the run around them of keys sharing d bits with key g; delta(g, j)
+// only falls as j moves away from g. A warp holds the keys of the 96
+// positions around its 32 points in registers (three coalesced loads per
+// lane), so four probes per point, taken by shuffles, decide most splits:
+// delta(g, g - 31) >= d or delta(g, g + 32) >= d means more than 32 points;
+// delta(g, g - 15) < d and delta(g, g + 16) < d means at most 30. For the
+// points left undecided the warp ballots, per point, which adjacent prefix
+// lengths of the window reach its d (the common prefix of sorted keys a < b
+// is the smallest adjacent one between them), and the run lengths to the
+// left and right follow from bit scans.
+constexpr int LEAF_T = TILE;
+static_assert(LEAF_T == 32, "the window holds 32 points on each side");
+
 template <typename K>
 __global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ dstart,
-                             const uint8_t* __restrict__ pdense, int64_t n, int T, int id_shift,
-                             int32_t* __restrict__ lf, const uint32_t* __restrict__ ctrl, int algo)
+                             const uint8_t* __restrict__ pdense, int64_t n, int id_shift, int32_t* __restrict__ lf,
+                             const uint32_t* __restrict__ ctrl, int algo)
 {
     if (!stage_on(ctrl, algo)) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int prev = (lane + 31) & 31;
+    for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {  // whole warps iterate together
+        // window: positions base - 32 + lane, base + lane, base + 32 + lane
+        const int64_t p0 = base - 32 + lane, p1 = base + lane, p2 = base + 32 + lane;
+        const K k0 = p0 >= 0 ? keys[p0] : K(0);  // (p0 < base < n)
+        const K k1 = p1 < n ? keys[p1] : K(0);
+        const K k2 = p2 < n ? keys[p2] : K(0);
+        // this lane's point i = p1 and split g = i - 1 (all lanes take part in
+        // every shuffle; lane-dependent sources pick the window segment)
+        const int64_t i = p1, g = i - 1;
+        K kg = shfl_key(k1, prev);
+        const K kg_first = shfl_key(k0, 31);
+        if (lane == 0) kg = kg_first;
+        const K kr_a = shfl_key(k2, prev), kr_b = shfl_key(k1, 31);      // g + 32
+        const K kl_a = shfl_key(k0, (lane + 16) & 31), kl_b = shfl_key(k1, (lane + 16) & 31);  // g - 15
+        const K km_a = shfl_key(k1, (lane + 15) & 31), km_b = shfl_key(k2, (lane + 15) & 31);  // g + 16
+        const K k_right32 = lane == 0 ? kr_b : kr_a;
+        const K k_left15 = lane < 16 ? kl_a : kl_b;
+        const K k_right16 = lane <= 16 ? km_a : km_b;
+        const bool generic = i < n && i > 0;
+        int d = -1;
+        int state = 0;  // 1 exceeds, 2 does not, 0 undecided
+        if (generic) {
+            d = key_delta(kg, g, k1, i, n);
+            if (key_delta(kg, g, k0, g - 31, n) >= d || key_delta(kg, g, k_right32, g + 32, n) >= d)
+                state = 1;
+            else if (key_delta(kg, g, k_left15, g - 15, n) < d && key_delta(kg, g, k_right16, g + 16, n) < d)
+                state = 2;
+        } else {
+            state = 2;
+        }
+        unsigned und = __ballot_sync(FULL, state == 0);
+        if (und) {
+            // adjacent prefix lengths of the window; -1 outside [0, n)
+            K n0 = shfl_key(k0, (lane + 1) & 31), n1 = shfl_key(k1, (lane + 1) & 31),
+              n2 = shfl_key(k2, (lane + 1) & 31);
+            const K f1 = shfl_key(k1, 0), f2 = shfl_key(k2, 0);
+            if (lane == 31) {
+                n0 = f1;
+                n1 = f2;
+                n2 = base + 64 < n ? keys[base + 64] : K(0);
+            }
+            const int w0 = p0 >= 0 ? key_delta(k0, p0, n0, p0 + 1, n) : -1;
+            const int w1 = p1 < n ? key_delta(k1, p1, n1, p1 + 1, n) : -1;
+            const int w2 = p2 < n ? key_delta(k2, p2, n2, p2 + 1, n) : -1;
+            uint32_t m0 = 0, m1 = 0, m2 = 0;
+            while (und) {
+                const int src = __ffs(und) - 1;
+                und &= und - 1;
+                const int ds = __shfl_sync(FULL, d, src);
+                const uint32_t b0 = __ballot_sync(FULL, w0 >= ds);
+                const uint32_t b1 = __ballot_sync(FULL, w1 >= ds);
+                const uint32_t b2 = __ballot_sync(FULL, w2 >= ds);
+                if (lane == src) {
+                    m0 = b0;
+                    m1 = b1;
+                    m2 = b2;
+                }
+            }
+            if (state == 0) {
+                // window index of g is lane + 31
+                const uint64_t lo = (uint64_t)m0 | ((uint64_t)m1 << 32), hi = m2;
+                const int pg = lane + 31;
+                const uint64_t below = ~lo & ((1ull << pg) - 1ull);
+                const int r_left = below ? pg - 1 - (63 - __clzll((long long)below)) : pg;
+                const uint64_t y = (lo >> (pg + 1)) | (hi << (63 - pg));
+                const int r_right = ~y ? __ffsll((long long)~y) - 1 : 64;
+                state = (r_left + r_right + 2) > LEAF_T ? 1 : 2;
+            }
+        }
+        if (i >= n) continue;
         int f;
         if (i == 0) f = 1;
-        else if (id_shift < 64 && (uint64_t)(keys[i] >> id_shift) != (uint64_t)(keys[i - 1] >> id_shift)) f = 1;
+        else if (id_shift < 64 && ((uint64_t)k1 >> id_shift) != ((uint64_t)kg >> id_shift)) f = 1;
         else if (pdense && pdense[i] == 2) f = dstart[i] == (int32_t)i ? 1 : 0;
         else if (pdense && pdense[i - 1] == 2) f = 1;
-        else f = radix_split_exceeds(keys, n, i - 1, T) ? 1 : 0;
+        else f = state == 1 ? 1 : 0;
         lf[i] = f;
     }
 }
@@ -758,7 +826,7 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
     GBD_DIM_SWITCH(dim, DC_LAUNCH)
 #undef DC_LAUNCH
     const int A = DBSCAN_ALGO_DENSEBOX;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, 64, t.lf, ctrl, A);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, 64, t.lf, ctrl, A);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, 64, leafr, lkey, nullptr, A);
@@ -774,7 +842,7 @@ cudaError_t launch_batch_leaves(const uint64_t* keys, int64_t n, int id_shift, c
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, TILE, id_shift, t.lf, ctrl, -1);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, id_shift, t.lf, ctrl, -1);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, -1);
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, id_shift, leafr, lkey, linst, -1);
@@ -788,7 +856,7 @@ cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBox
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
     const int A = DBSCAN_ALGO_FDBSCAN;
-    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, TILE, 64, t.lf, ctrl, A);
+    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, 64, t.lf, ctrl, A);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
     k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, 64, leafr, lkey, nullptr, A);
@@ -802,7 +870,7 @@ cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBox
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
     const int A = DBSCAN_ALGO_FDBSCAN;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, nullptr, nullptr, n, TILE, 64, t.lf, ctrl, A);
+    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, nullptr, nullptr, n, 64, t.lf, ctrl, A);
     if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
     k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys, ctrl, 64, leafr, lkey, nullptr, A);

@@ -431,7 +431,10 @@ struct PreV {
     // list entries are worth a first test against the box of the active queries
     static constexpr bool PREFILTER = true;
     static constexpr bool NEEDS_SOLID = false;
-    __device__ __forceinline__ typename T::Box query_box() const { return warp_box<D>(p, act); }
+    // the box of the queries active when the walk starts (set before it;
+    // queries only drop out, so it stays a bound for those still counting)
+    typename T::Box qbox;
+    __device__ __forceinline__ typename T::Box query_box() const { return qbox; }
 
     __device__ __forceinline__ bool leaf(int L, unsigned mask, const typename T::Box& box)
     {
@@ -593,7 +596,8 @@ struct MainPtV {
     __device__ __forceinline__ bool hit_box(const typename T::Box& b) const { return valid && NB<D>::pbox(p, b) <= e2; }
     static constexpr bool PREFILTER = true;
     static constexpr bool NEEDS_SOLID = true;
-    __device__ __forceinline__ typename T::Box query_box() const { return warp_box<D>(p, valid); }
+    typename T::Box qbox;  // the box of the valid queries (set before the walk)
+    __device__ __forceinline__ typename T::Box query_box() const { return qbox; }
     __device__ __forceinline__ unsigned root_mask() const { return __ballot_sync(FULL, valid); }
 
     __device__ __forceinline__ bool leaf(int L, unsigned mask, const typename T::Box& box)
@@ -651,18 +655,27 @@ struct MainPtV {
         const bool need = ((mask >> lane) & 1u) && rule.need_solid(q, qcore, s);
         if (need && cont) rule.join_solid(q, qcore, s);
         unsigned nm = __ballot_sync(FULL, need && !cont);
-        while (nm) {
-            const int qq = __ffs(nm) - 1;
-            nm &= nm - 1;
-            const P pq = NB<D>::shfl(p, qq);
-            bool found = false;
-            for (int c = s; c < e; c += 32) {
+        if (nm) {
+            // the leaf's points in chunks, each pruned to those within eps of
+            // the box of the queries (exact, reading 3); each query still
+            // looking is tested against the survivors until it finds one
+            for (int c = s; c < e && nm; c += 32) {
                 const int j = c + lane;
-                const bool h = j < e && dist2(pq, sp[j]) <= e2;
-                if (__any_sync(FULL, h)) { found = true; break; }
+                const P rp = j < e ? sp[j] : sp[c];
+                const bool keep = j < e && NB<D>::pbox(rp, qbox) <= e2;
+                if (!__any_sync(FULL, keep)) continue;
+                unsigned mm = nm;
+                while (mm) {
+                    const int qq = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const P pq = NB<D>::shfl(p, qq);
+                    if (__any_sync(FULL, keep && dist2(pq, rp) <= e2)) {
+                        if (lane == qq) rule.join_solid(q, qcore, s);
+                        nm &= ~(1u << qq);
+                    }
+                }
+                __syncwarp();
             }
-            if (found && lane == qq) rule.join_solid(q, qcore, s);
-            __syncwarp();
         }
         return false;
     }
@@ -712,25 +725,32 @@ struct MainSolidV {
             int same = 0;
             if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
             if (__shfl_sync(FULL, same, 0)) return false;
-            bool found = __any_sync(FULL, ((mask >> lane) & 1u) && T::far_dist2(p, box) <= e2);
+            const bool act = (mask >> lane) & 1u;
+            bool found = __any_sync(FULL, act && T::far_dist2(p, box) <= e2);
+            // only the leaf's points within eps of this tile's box can be
+            // partners (exact pruning, reading 3)
+            const unsigned lt = (1u << lane) - 1u;
             for (int c = s; c < e && !found; c += 32) {
                 const int k = min(32, e - c);
-                if (__popc(mask) < k) {
-                    const bool in = lane < k;
-                    const P rp = in ? sp[c + lane] : sp[c];
+                const P rp = lane < k ? sp[c + lane] : sp[c];
+                const bool keep = lane < k && NB<D>::pbox(rp, qb) <= e2;
+                const unsigned km = __ballot_sync(FULL, keep);
+                if (!km) continue;
+                const int kk = __popc(km);
+                if (__popc(mask) < kk) {
                     unsigned mm = mask;
                     while (mm && !found) {
                         const int qq = __ffs(mm) - 1;
                         mm &= mm - 1;
                         const P pq = NB<D>::shfl(p, qq);
-                        found = __any_sync(FULL, in && dist2(pq, rp) <= e2);
+                        found = __any_sync(FULL, keep && dist2(pq, rp) <= e2);
                     }
                 } else {
-                    if (lane < k) buf[lane] = sp[c + lane];
+                    if (keep) buf[__popc(km & lt)] = rp;
                     __syncwarp();
                     bool h = false;
-                    if ((mask >> lane) & 1u)
-                        for (int u = 0; u < k; ++u)
+                    if (act)
+                        for (int u = 0; u < kk; ++u)
                             if (dist2(p, buf[u]) <= e2) { h = true; break; }
                     __syncwarp();
                     found = __any_sync(FULL, h);
@@ -800,23 +820,35 @@ struct MainBoxV {
         if (L < mask_lo || L % parts != part) return false;
         const int2 r = __ldg(&leafr[L]);
         const int s = r.x, e = r.y & 0x7fffffff;
+        const unsigned lt = (1u << lane) - 1u;
         if (lsolid[L]) {
             // solid against solid: any adjacent cross pair unites the two sets
             int same = 0;
             if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
             if (__shfl_sync(FULL, same, 0)) return false;
             bool found = T::box_far2(qb, box) <= e2;
+            // only the cell's points within eps of the other leaf's box can
+            // have a partner there, and of the other leaf only the points
+            // within eps of the cell's box (exact pruning, reading 3); the
+            // survivors are compacted into the staging buffer
             for (int cq = sQ; cq < eQ && !found; cq += 32) {
                 const int iq = cq + lane;
                 const bool inq = iq < eQ;
                 const P pq = inq ? sp[iq] : sp[sQ];
+                const bool near = inq && NB<D>::pbox(pq, box) <= e2;
+                if (!__any_sync(FULL, near)) continue;
                 for (int c = s; c < e; c += 32) {
                     const int k = min(32, e - c);
-                    if (lane < k) buf[lane] = sp[c + lane];
+                    const P rp = lane < k ? sp[c + lane] : sp[c];
+                    const bool keep = lane < k && NB<D>::pbox(rp, qb) <= e2;
+                    const unsigned km = __ballot_sync(FULL, keep);
+                    if (!km) continue;
+                    if (keep) buf[__popc(km & lt)] = rp;
                     __syncwarp();
+                    const int kk = __popc(km);
                     bool h = false;
-                    if (inq)
-                        for (int u = 0; u < k; ++u)
+                    if (near)
+                        for (int u = 0; u < kk; ++u)
                             if (dist2(pq, buf[u]) <= e2) { h = true; break; }
                     __syncwarp();
                     if (__any_sync(FULL, h)) { found = true; break; }
@@ -826,7 +858,8 @@ struct MainBoxV {
             __syncwarp();
             return false;
         }
-        // a tile that is not solid: one lane per tile point
+        // a tile that is not solid: one lane per tile point, against the
+        // cell's points within eps of the tile's box
         const int k = e - s;
         const bool in = lane < k;
         const int ri = s + lane;
@@ -834,15 +867,22 @@ struct MainBoxV {
         const bool rc = in && core[ri];
         const bool need = in && rule.need_solid(ri, rc, sQ);
         bool found = need && T::far_dist2(rp, qb) <= e2;
-        for (int cq = sQ; cq < eQ; cq += 32) {
-            if (!__any_sync(FULL, need && !found)) break;
-            const int kq = min(32, eQ - cq);
-            if (lane < kq) buf[lane] = sp[cq + lane];
-            __syncwarp();
-            if (need && !found)
-                for (int u = 0; u < kq; ++u)
-                    if (dist2(rp, buf[u]) <= e2) { found = true; break; }
-            __syncwarp();
+        if (__any_sync(FULL, need && !found)) {
+            for (int cq = sQ; cq < eQ; cq += 32) {
+                if (!__any_sync(FULL, need && !found)) break;
+                const int kq = min(32, eQ - cq);
+                const P ap = lane < kq ? sp[cq + lane] : sp[sQ];
+                const bool keep = lane < kq && NB<D>::pbox(ap, box) <= e2;
+                const unsigned km = __ballot_sync(FULL, keep);
+                if (!km) continue;
+                if (keep) buf[__popc(km & lt)] = ap;
+                __syncwarp();
+                const int kk = __popc(km);
+                if (need && !found)
+                    for (int u = 0; u < kk; ++u)
+                        if (dist2(rp, buf[u]) <= e2) { found = true; break; }
+                __syncwarp();
+            }
         }
         if (need && found) rule.join_solid(ri, rc, sQ);
         __syncwarp();
@@ -1163,7 +1203,10 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_pre(DevArgs<D> a)
         v.lcap = a.lcap;
         v.qs = s;
         v.nl = 0;
-        if (__any_sync(FULL, v.act)) walk(a, m, v, wm->stack, L);
+        if (__any_sync(FULL, v.act)) {
+            v.qbox = warp_box<D>(p, v.act);
+            walk(a, m, v, wm->stack, L);
+        }
         if (counts) {
             const bool c = v.cnt >= tp.min_pts;
             a.core[q] = c ? 1 : 0;
@@ -1375,7 +1418,10 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
             v.valid = in && (tp.min_pts <= 2 || v.qcore || (rule.claims && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
             v.pp = NB<D>::pack(v.p);
-            if (__any_sync(FULL, v.valid)) walk(a, m, v, wm->stack, L);
+            if (__any_sync(FULL, v.valid)) {
+                v.qbox = warp_box<D>(v.p, v.valid);
+                walk(a, m, v, wm->stack, L);
+            }
         } else if (KIND == 1) {
             MainSolidV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
