@@ -310,6 +310,8 @@ def run_gb300(args, rank: int, world: int) -> None:
                 "traffic_source": "profiles/preprocess_main_densebox_halos8m.md (8M capture scaled by points)"
                 if traffic is not None else None}
 
+    small = small_job_figures(args, dev) if (rank == 0 and not args.no_small_jobs) else {}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         W = cpu_sample(X, args.cpu_side)
@@ -337,11 +339,159 @@ def run_gb300(args, rank: int, world: int) -> None:
             "hbm_frac_path": path_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
             "features_per_s": value * d,
             "stats": stats,
+            **small,
         }
         print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------ batch and serve
+SMALL_BATCH = 512
+SMALL_SERVE_JOBS = 400
+SMALL_SERVE_RATES = (1000.0, 3000.0, 30000.0)
+SMALL_SERVE_SIZES = (10_000, 262_144)
+
+
+def small_job_figures(args, dev) -> dict:
+    """Batched and served small jobs on one GPU, at reduced sizes that fit
+    the default run (the full batch and serving sweeps are --mode batch and
+    --mode serve):
+    * batched: SMALL_BATCH instances of the batch family in one fused
+      dbscan_run_batch (graph-captured once the shape repeats) against one
+      dbscan_run per instance enqueued back to back on one stream;
+    * served: Poisson traces of SMALL_SERVE_JOBS jobs of 10K-256K points
+      through the server (continuous batching) against one dbscan_run per
+      job in arrival order, each waited for (a one-job-at-a-time server).
+    Latencies are wall clock, arrival (or call) to labels complete."""
+    import torch
+
+    import paper_2103_05162_gb300 as gb
+    from workloads import batch_instances, serve_pools, serve_schedule
+
+    out = {}
+    # ---- batched
+    inst = batch_instances(SMALL_BATCH, args.seed + 1)
+    flat = np.concatenate([x.points.ravel() for x in inst]).astype(np.float32)
+    offs = np.concatenate([[0], np.cumsum([x.n for x in inst])]).astype(np.int64)
+    coffs = np.concatenate([[0], np.cumsum([x.n * x.dim for x in inst])]).astype(np.int64)
+    dims, eps, mps = [x.dim for x in inst], [x.eps for x in inst], [x.min_pts for x in inst]
+    pts = torch.from_numpy(flat).to(dev)
+    total = int(offs[-1])
+    labels = torch.empty(total, dtype=torch.int32, device=dev)
+    views = [pts[coffs[b]:coffs[b + 1]].view(-1, dims[b]) for b in range(len(inst))]
+    outs = [labels[offs[b]:offs[b + 1]] for b in range(len(inst))]
+
+    def fused():
+        gb.dbscan_run_batch(pts, offs, dims, eps, mps, algo=gb.ALGO_DENSEBOX, labels_out=labels)
+
+    def sequential():
+        for b in range(len(inst)):
+            gb.dbscan_run(views[b], eps[b], mps[b], algo=gb.ALGO_DENSEBOX, labels_out=outs[b])
+
+    for _ in range(3):  # direct launch, capture, replay
+        fused()
+    sequential()
+    torch.cuda.synchronize(dev)
+    tf, tsq = [], []
+    for _ in range(7):
+        t = time.perf_counter()
+        fused()
+        torch.cuda.synchronize(dev)
+        tf.append(time.perf_counter() - t)
+    for _ in range(3):
+        t = time.perf_counter()
+        sequential()
+        torch.cuda.synchronize(dev)
+        tsq.append(time.perf_counter() - t)
+    gb.stream_status()
+    f50, sq = float(np.median(tf)), float(np.median(tsq))
+    out["batched"] = {
+        "workload": f"{SMALL_BATCH} instances of the batch family (lognormal sizes, median 20k, sigma 1.2, "
+                    "clipped to [1k, 500k]; 2D/3D blobs; eps U[0.01,0.05]; minPts U{2,5,10}), DenseBox, DBSCAN",
+        "points": total, "instances": len(inst),
+        "p50_ms": 1e3 * f50, "p99_ms": 1e3 * float(np.percentile(tf, 99)),
+        "points_per_s": total / f50,
+        "sequential": {"ms": 1e3 * sq, "points_per_s": total / sq},
+        "ratio": sq / f50,
+    }
+    del pts, labels, views, outs
+
+    # ---- served
+    pool_n = 1 << 20
+    pools = {k: torch.from_numpy(v).to(dev) for k, v in serve_pools(pool_n, args.seed + 100).items()}
+    scheds = [serve_schedule(SMALL_SERVE_JOBS, lam, args.seed + 2000 + i, pool_n=pool_n,
+                             size_range=SMALL_SERVE_SIZES) for i, lam in enumerate(SMALL_SERVE_RATES)]
+    cap = max(sum(j.n for j in sc) for sc in scheds)
+    arena = torch.empty(cap, dtype=torch.int32, device=dev)
+    srv = gb.Server(int(args.serve_budget_gb * (1 << 30)), max_slots=args.serve_slots)
+
+    def views_of(sched):
+        res, o = [], 0
+        for j in sched:
+            res.append((pools[j.pool][j.offset:j.offset + j.n], arena[o:o + j.n]))
+            o += j.n
+        return res
+
+    def served(sched, vs):
+        lag, ids, sub = [], [], []
+        t0 = time.perf_counter()
+        for j, (x, lab) in zip(sched, vs):
+            target = t0 + j.arrival_s
+            now = _wait_until(target)
+            ids.append(srv.submit(x, j.eps, j.min_pts, algo=j.algo, labels_out=lab))
+            lag.append(now - target)
+            sub.append(now)
+        lat, done_at = [], []
+        for jid, lg, ts in zip(ids, lag, sub):
+            srv.wait(jid, timeout=600)
+            _, l_srv = srv.poll(jid)
+            srv.release(jid)
+            lat.append(lg + l_srv)
+            done_at.append(ts + l_srv)
+        return np.asarray(lat), max(done_at) - t0
+
+    def one_at_a_time(sched, vs):
+        lat, t0 = [], time.perf_counter()
+        done = t0
+        for j, (x, lab) in zip(sched, vs):
+            target = t0 + j.arrival_s
+            _wait_until(max(target, done))
+            gb.dbscan_run(x, j.eps, j.min_pts, algo=j.algo, labels_out=lab)
+            torch.cuda.synchronize(dev)
+            done = time.perf_counter()
+            lat.append(done - target)
+        return np.asarray(lat), done - t0
+
+    rows = []
+    for lam, sched in zip(SMALL_SERVE_RATES, scheds):
+        vs = views_of(sched)
+        pts_total = sum(j.n for j in sched)
+        served(sched, vs)  # warm-up: workspaces, graphs
+        one_at_a_time(sched, vs)
+        stats0 = srv.stats()
+        lat, span = served(sched, vs)
+        st = {k: v - stats0[k] for k, v in srv.stats().items()}
+        slat, sspan = one_at_a_time(sched, vs)
+        rows.append({
+            "rate_per_s": lam, "jobs": len(sched), "points": pts_total,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "points_per_s": pts_total / span,
+            "sequential": {"p50_ms": 1e3 * float(np.percentile(slat, 50)),
+                           "p99_ms": 1e3 * float(np.percentile(slat, 99)), "points_per_s": pts_total / sspan},
+            "ratio": sspan / span, "fused_batches": st.get("batches"), "fused_jobs": st.get("batched_jobs"),
+        })
+    srv.close()
+    gb.stream_status()
+    out["served"] = {
+        "workload": f"Poisson arrivals, {SMALL_SERVE_JOBS} jobs per rate, sizes log-uniform on "
+                    f"[{SMALL_SERVE_SIZES[0]}, {SMALL_SERVE_SIZES[1]}], families blobs3/roads/halos/batch "
+                    "instance (windows of 1M-point shuffled pools), DBSCAN mode; "
+                    f"server: {args.serve_slots} slots, {args.serve_budget_gb} GB budget; sequential: "
+                    "one dbscan_run per job in arrival order, each waited for",
+        "rates": rows,
+    }
+    return out
+
+
 def run_batch_mode(args) -> None:
     """One fused dbscan_run_batch over thousands of independent instances
     against one dbscan_run per instance on one stream (same inputs, same
@@ -590,6 +740,7 @@ def main():
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-small-jobs", action="store_true", help="skip the batched / served small-job figures")
     ap.add_argument("--border-lists", type=int, choices=[0, 1], default=None,
                     help="border claims from per-point neighbour lists (1) or in the main traversal (0); "
                          "default: the library's default")
