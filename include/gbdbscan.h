@@ -237,10 +237,32 @@ const char* dbscan_last_error(void);
 
 /*
  * Tuning knobs (process-wide): traversal block size in threads (a multiple of
- * 32 up to 1024; 0 = default) and the DenseBox cell-side factor f in (0, 1]
- * (cell side f*eps/sqrt(dim); 0 = default 1). Results do not depend on them.
+ * 32 up to 1024) and the DenseBox cell-side factor f in (0, 1] (cell side
+ * f*eps/sqrt(dim); Sec. 4.2 uses f = 1). Results do not depend on them.
+ * 0 = autotune (the default for both): the first dbscan_run,
+ * dbscan_run_sync, dbscan_run_host or dbscan_run_batch call of each kind --
+ * dimension, ceil(log2 n), minPts, algorithm and mode (and ceil(log2 count)
+ * for batches) -- measures block sizes {64, 128, 256} x factors
+ * {1, 0.75, 0.5} (FDbscan: block sizes only; a fixed knob keeps its value)
+ * on the caller's own data, a few runs each, keeps the fastest in a table
+ * and uses it for every later call of that kind. That first call waits for
+ * the stream (like workspace growth) and returns device-side errors at once;
+ * later calls do not wait. The server, dbscan_run_multi and
+ * dbscan_run_slabs use the table's entry when there is one, else block 128
+ * and f = 1, and never measure.
  */
 dbscan_status dbscan_set_tuning(int block_size, float cell_factor);
+
+/*
+ * The autotuner's entry for a kind of call (batch = 0: dbscan_run with dim,
+ * n, min_pts; batch = 1: dbscan_run_batch with n = total points, min_pts =
+ * the largest, count instances): block size, cell factor and the measured
+ * milliseconds per call (ms_out may be NULL). DBSCAN_ERR_NOT_FOUND when that
+ * kind has not been tuned. dbscan_tuning_clear() empties the table.
+ */
+dbscan_status dbscan_tuning_lookup(int batch, int dim, int64_t n, int min_pts, int mode, int algo, int64_t count,
+                                   int* block_out, float* cell_factor_out, float* ms_out);
+dbscan_status dbscan_tuning_clear(void);
 
 /*
  * How border points join a cluster in DBSCAN mode (Sec. 3.2, Algorithm 3:

@@ -98,6 +98,9 @@ def load(build_if_missing: bool = True):
             "dbscan_last_stats": [vp, vp],
             "dbscan_test_sort_hooks": [i64, i32],
             "dbscan_set_border_lists": [i32],
+            "dbscan_tuning_lookup": [i32, i32, i64, i32, i32, i32, i64, ctypes.POINTER(i32),
+                                     ctypes.POINTER(f32), ctypes.POINTER(f32)],
+            "dbscan_tuning_clear": [],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -418,6 +421,24 @@ def sort_test_hooks(wait_limit: int = -1, stall_first_tile: bool = False):
     """Test hooks of the radix sort's bounded wait (see dbscan_test_sort_hooks);
     (-1, False) restores the defaults."""
     _check(load().dbscan_test_sort_hooks(int(wait_limit), 1 if stall_first_tile else 0))
+
+
+def tuning_lookup(dim: int, n: int, min_pts: int, mode="dbscan", algo="densebox", batch: bool = False,
+                  count: int = 0):
+    """The autotuner's (block size, cell factor, ms per call) for a kind of
+    call, or None if that kind has not been tuned (see dbscan_tuning_lookup)."""
+    lib = load()
+    b, f, ms = ctypes.c_int(), ctypes.c_float(), ctypes.c_float()
+    st = lib.dbscan_tuning_lookup(1 if batch else 0, int(dim), int(n), int(min_pts), _mode(mode), _algo(algo),
+                                  int(count), ctypes.byref(b), ctypes.byref(f), ctypes.byref(ms))
+    if st == 7:  # NOT_FOUND
+        return None
+    _check(st)
+    return b.value, f.value, ms.value
+
+
+def tuning_clear():
+    _check(load().dbscan_tuning_clear())
 
 
 def set_tuning(block_size: int = 0, cell_factor: float = 0.0):

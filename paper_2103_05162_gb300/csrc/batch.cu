@@ -464,7 +464,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
     a.e2 = 0.0f;
     a.min_pts = max_mp;
     a.mode = mode;
-    a.block = g_tuning.block;
+    a.block = t_run.block;
     a.linst = p.linst;
     a.e2s = p.e2s;
     a.mps = p.mps;
@@ -559,7 +559,7 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
         if (algo == DBSCAN_ALGO_FDBSCAN) {
             bits = 10 < max_axis_bits ? 10 : max_axis_bits;
         } else {
-            const double h = (double)g_tuning.cell_factor * (double)eps[b] / std::sqrt((double)dims[b]);
+            const double h = (double)t_run.cell_factor * (double)eps[b] / std::sqrt((double)dims[b]);
             hcell[b] = h;
             const double cells = std::floor(ext / h) + 1.0;
             while (bits < max_axis_bits && std::ldexp(1.0, bits) < cells + 1.0) ++bits;
@@ -615,7 +615,7 @@ dbscan_status run_batch(Workspace* w, int32_t count, const int64_t* offsets, con
     shape.lb = lb;
     shape.key_bits = key_bits;
     shape.max_mp = max_mp;
-    shape.block = g_tuning.block;
+    shape.block = t_run.block;
     const bool replay = g->exec && g->captured == shape;
     const bool capture = !replay && g->last == shape;
     g->last = shape;

@@ -47,14 +47,95 @@ dbscan_status cuda_error(cudaError_t e, const char* what)
     } while (0)
 
 // (above 3D the 3D thresholds: FDbscan's Morton grid is coarse there too)
-Tuning g_tuning = {128,
-                   1.0f,
+Tuning g_tuning = {0,
+                   0.0f,
                    1,
                    {0.0f, 0.0f, DEFAULT_AUTO_FRACTION_2D, DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D,
                     DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D, DEFAULT_AUTO_FRACTION_3D,
                     DEFAULT_AUTO_FRACTION_3D},
                    {0.0f, 0.0f, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY,
                     DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY, DEFAULT_AUTO_OCCUPANCY}};
+
+// ---------------------------------------------------------------------------
+// the autotuner's table (traversal block size and DenseBox cell factor per
+// kind of call)
+// ---------------------------------------------------------------------------
+thread_local RunTuning t_run = DEFAULT_RUN_TUNING;
+
+bool TuneKey::operator<(const TuneKey& o) const
+{
+    const int a[7] = {kind, dim, log2n, min_pts, algo, mode, log2count};
+    const int b[7] = {o.kind, o.dim, o.log2n, o.min_pts, o.algo, o.mode, o.log2count};
+    for (int i = 0; i < 7; ++i)
+        if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+}
+
+static int ceil_log2(int64_t v)
+{
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+TuneKey tune_key(int kind, int dim, int64_t n, int min_pts, int algo, int mode, int64_t count)
+{
+    return TuneKey{kind, dim, ceil_log2(n), min_pts, algo, mode, kind == 1 ? ceil_log2(count) : 0};
+}
+
+namespace {
+struct TuneEntry {
+    RunTuning t;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+}  // namespace
+
+bool autotune_on() { return g_tuning.block == 0 || g_tuning.cell_factor == 0.0f; }
+
+bool tuned(const TuneKey& k)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_tune.count(k) != 0;
+}
+
+void store_tuning(const TuneKey& k, RunTuning t, float ms)
+{
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[k] = TuneEntry{t, ms};
+}
+
+RunTuning resolve_tuning(const TuneKey& k)
+{
+    RunTuning r = DEFAULT_RUN_TUNING;
+    if (autotune_on()) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(k);
+        if (it != g_tune.end()) r = it->second.t;
+    }
+    if (g_tuning.block != 0) r.block = g_tuning.block;
+    if (g_tuning.cell_factor != 0.0f) r.cell_factor = g_tuning.cell_factor;
+    return r;
+}
+
+int tuning_candidates(int algo, RunTuning* out, int cap)
+{
+    static const int blocks[3] = {64, 128, 256};
+    static const float factors[3] = {1.0f, 0.75f, 0.5f};
+    const int nf = algo == DBSCAN_ALGO_FDBSCAN ? 1 : 3;  // FDbscan has no grid
+    int k = 0;
+    for (int i = 0; i < nf; ++i) {
+        const float f = g_tuning.cell_factor != 0.0f ? g_tuning.cell_factor : factors[i];
+        for (int j = 0; j < 3; ++j) {
+            const int b = g_tuning.block != 0 ? g_tuning.block : blocks[j];
+            bool dup = false;
+            for (int t = 0; t < k; ++t) dup = dup || (out[t].block == b && out[t].cell_factor == f);
+            if (!dup && k < cap) out[k++] = RunTuning{b, f};
+        }
+    }
+    return k;
+}
 
 // ---------------------------------------------------------------------------
 // launch counting and opt-in per-stage timing (CUDA events on the stream)
@@ -159,7 +240,8 @@ struct Plan {
     int32_t* nlist;  // n * lcap neighbour indices (preprocessing lists)
     int32_t* ncount; // n neighbour counts capped at the largest minPts (multi-minPts runs)
     EstBuffers est;  // density estimate (automatic algorithm choice)
-    GridParams* grid; // DenseBox grid, computed on the device from the bounds
+    GridParams* grid;     // DenseBox grid, computed on the device from the bounds
+    GridParams* grid_est; // the automatic choice's grid (cell side eps / sqrt(d), whatever the tuning)
 };
 
 int64_t leaf_cap(int64_t n, int algo)
@@ -231,6 +313,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.est.counts = c.take<uint32_t>(EST_SLOTS);
     p.est.result = c.take<uint32_t>(4);
     p.grid = c.take<GridParams>(1);
+    p.grid_est = c.take<GridParams>(1);
     return c.off + 256;
 }
 
@@ -403,10 +486,14 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     const int idx_bits = index_bits(n);
     const int db_axis_bits = densebox_axis_bits(dim, idx_bits);
     const int db_key_bits = db_axis_bits * dim;
-    if (db) launch_grid(p.ctrl, dim, eps, g_tuning.cell_factor, db_axis_bits, p.grid, s);
-    if (algo == DBSCAN_ALGO_AUTO)
-        TRY_CUDA(launch_density_estimate(points, n, dim, p.grid, dense_mp, g_tuning.auto_fraction[dim],
+    if (algo == DBSCAN_ALGO_AUTO) {
+        // the estimate's thresholds belong to the cells of Sec. 4.2 (f = 1)
+        launch_grid(p.ctrl, dim, eps, 1.0f, db_axis_bits, p.grid_est, s);
+        TRY_CUDA(launch_density_estimate(points, n, dim, p.grid_est, dense_mp, g_tuning.auto_fraction[dim],
                                          g_tuning.auto_occupancy[dim], p.est, p.ctrl, s));
+    }
+    // (after the estimate's grid: CTRL_KEYBITS is this grid's)
+    if (db) launch_grid(p.ctrl, dim, eps, t_run.cell_factor, db_axis_bits, p.grid, s);
 
     SortBuffers sb;
     sb.keys_alt = p.keys_alt;
@@ -518,7 +605,7 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     a.m_cap = m_cap;
     a.dim = dim;
     a.e2 = e2;
-    a.block = g_tuning.block;
+    a.block = t_run.block;
     return DBSCAN_OK;
 }
 
@@ -687,6 +774,65 @@ dbscan_status workspace_status(Workspace* w, cudaStream_t s)
 
 }  // namespace gbd
 
+namespace gbd {
+
+// The autotuner for one kind of dbscan_run call: the candidates are measured
+// on the caller's own data (one warm-up run and two timed runs each, CUDA
+// events on the stream), the fastest is stored for the key and left in
+// t_run. Waits for the stream (the first call of a key is a sync point);
+// device-side errors of the data are returned here.
+dbscan_status autotune_single(Workspace* w, const TuneKey& key, const float* points, int64_t n, int dim, float eps,
+                              int min_pts, int mode, int algo, int32_t* labels_out, uint8_t* core_out,
+                              cudaStream_t s)
+{
+    RunTuning cand[16];
+    const int nc = tuning_candidates(algo, cand, 16);
+    cudaEvent_t a = nullptr, b = nullptr;
+    TRY_CUDA(cudaEventCreate(&a));
+    TRY_CUDA(cudaEventCreate(&b));
+    float best = 3.0e38f;
+    RunTuning bt = DEFAULT_RUN_TUNING;
+    dbscan_status st = DBSCAN_OK;
+    for (int i = 0; i < nc && st == DBSCAN_OK; ++i) {
+        t_run = cand[i];
+        st = run_pipeline(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+        if (st != DBSCAN_OK) break;
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 2 && st == DBSCAN_OK; ++r)
+            st = run_pipeline(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+        cudaEventRecord(b, s);
+        if (st != DBSCAN_OK) break;
+        st = workspace_status(w, s);
+        if (st != DBSCAN_OK) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            bt = cand[i];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != DBSCAN_OK) return st;
+    store_tuning(key, bt, best / 2.0f);
+    t_run = bt;
+    return DBSCAN_OK;
+}
+
+// the tuning of one dbscan_run call: measured now if the autotuner is on and
+// the key is new, else from the table (or the fixed knobs)
+dbscan_status prepare_single(Workspace* w, const float* points, int64_t n, int dim, float eps, int min_pts, int mode,
+                             int algo, int32_t* labels_out, uint8_t* core_out, cudaStream_t s)
+{
+    const TuneKey key = tune_key(0, dim, n, min_pts, algo, mode, 0);
+    if (autotune_on() && !tuned(key))
+        return autotune_single(w, key, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+    t_run = resolve_tuning(key);
+    return DBSCAN_OK;
+}
+
+}  // namespace gbd
+
 extern "C" {
 
 dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
@@ -699,6 +845,8 @@ dbscan_status dbscan_run(const float* points, int64_t n, int dim, float eps, int
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    st = prepare_single(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
+    if (st != DBSCAN_OK) return st;
     return run_pipeline(w, points, n, dim, eps, min_pts, mode, algo, labels_out, core_out, s);
 }
 
@@ -726,6 +874,9 @@ dbscan_status dbscan_run_multi(const float* points, int64_t n, int dim, float ep
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    int max_mp = 1;
+    for (int32_t k = 0; k < count; ++k) max_mp = min_pts[k] > max_mp ? min_pts[k] : max_mp;
+    t_run = resolve_tuning(tune_key(0, dim, n, max_mp, algo, mode, 0));
     return run_multi(w, points, n, dim, eps, min_pts, count, mode, algo, labels_out, core_out, s);
 }
 
@@ -745,6 +896,8 @@ dbscan_status dbscan_run_slabs(const float* points_host, int64_t n, int dim, flo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    t_run = resolve_tuning(tune_key(0, dim, slab_points > 0 && slab_points < n ? slab_points : n, min_pts, algo,
+                                    mode, 0));
     return run_slabs(w, points_host, n, dim, eps, min_pts, mode, algo, labels_host, core_host,
                      slab_points > 0 ? slab_points : (int64_t(1) << 26), s);
 }
@@ -768,6 +921,8 @@ dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, floa
     int32_t* dlab = reinterpret_cast<int32_t*>(base + ((pbytes + 255) & ~size_t(255)));
     uint8_t* dcore = reinterpret_cast<uint8_t*>(base + ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)));
     TRY_CUDA(cudaMemcpyAsync(dpts, points_host, pbytes, cudaMemcpyHostToDevice, s));
+    st = prepare_single(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
+    if (st != DBSCAN_OK) return st;
     st = run_pipeline(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
     if (st != DBSCAN_OK) return st;
     TRY_CUDA(cudaMemcpyAsync(labels_host, dlab, lbytes, cudaMemcpyDeviceToHost, s));
@@ -812,6 +967,45 @@ dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, cons
         cp[b] = core_out ? core_out + offsets[b] : nullptr;
         coff += (offsets[b + 1] - offsets[b]) * dims[b];
     }
+    int max_mp = 1;
+    for (int32_t b = 0; b < count; ++b) max_mp = min_pts[b] > max_mp ? min_pts[b] : max_mp;
+    const TuneKey key = tune_key(1, 0, offsets[count], max_mp, algo, mode, count);
+    if (autotune_on() && !tuned(key) && offsets[count] > 0) {
+        // the autotuner for this kind of batch: each candidate is launched
+        // directly, captured and replayed; the replay is timed
+        RunTuning cand[16];
+        const int nc = tuning_candidates(algo, cand, 16);
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        TRY_CUDA(cudaEventCreate(&ea));
+        TRY_CUDA(cudaEventCreate(&eb));
+        float best = 3.0e38f;
+        RunTuning bt = DEFAULT_RUN_TUNING;
+        dbscan_status st = DBSCAN_OK;
+        for (int i = 0; i < nc && st == DBSCAN_OK; ++i) {
+            t_run = cand[i];
+            for (int r = 0; r < 2 && st == DBSCAN_OK; ++r)
+                st = run_batch(w, count, offsets, pp.data(), dims, eps, min_pts, lp.data(),
+                               core_out ? cp.data() : nullptr, mode, algo, s);
+            if (st != DBSCAN_OK) break;
+            cudaEventRecord(ea, s);
+            st = run_batch(w, count, offsets, pp.data(), dims, eps, min_pts, lp.data(), core_out ? cp.data() : nullptr,
+                           mode, algo, s);
+            cudaEventRecord(eb, s);
+            if (st == DBSCAN_OK) st = workspace_status(w, s);
+            if (st != DBSCAN_OK) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ea, eb);
+            if (ms < best) {
+                best = ms;
+                bt = cand[i];
+            }
+        }
+        cudaEventDestroy(ea);
+        cudaEventDestroy(eb);
+        if (st != DBSCAN_OK) return st;
+        store_tuning(key, bt, best);
+    }
+    t_run = resolve_tuning(key);
     return run_batch(w, count, offsets, pp.data(), dims, eps, min_pts, lp.data(), core_out ? cp.data() : nullptr,
                      mode, algo, s);
 }
@@ -951,8 +1145,31 @@ dbscan_status dbscan_set_tuning(int block_size, float cell_factor)
         return set_error(DBSCAN_ERR_INVALID_ARG, "block size must be a multiple of 32 in [32, 1024]");
     if (cell_factor != 0.0f && !(cell_factor > 0.0f && cell_factor <= 1.0f))
         return set_error(DBSCAN_ERR_INVALID_ARG, "cell factor must be in (0, 1]");
-    g_tuning.block = block_size ? block_size : 128;
-    g_tuning.cell_factor = cell_factor != 0.0f ? cell_factor : 1.0f;
+    g_tuning.block = block_size;
+    g_tuning.cell_factor = cell_factor;
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_tuning_lookup(int batch, int dim, int64_t n, int min_pts, int mode, int algo, int64_t count,
+                                   int* block_out, float* cell_factor_out, float* ms_out)
+{
+    t_err.clear();
+    if (!block_out || !cell_factor_out) return set_error(DBSCAN_ERR_INVALID_ARG, "null argument");
+    const TuneKey key = tune_key(batch ? 1 : 0, batch ? 0 : dim, n, min_pts, algo, mode, count);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return set_error(DBSCAN_ERR_NOT_FOUND, "no autotuned entry for this kind of call");
+    *block_out = it->second.t.block;
+    *cell_factor_out = it->second.t.cell_factor;
+    if (ms_out) *ms_out = it->second.ms;
+    return DBSCAN_OK;
+}
+
+dbscan_status dbscan_tuning_clear(void)
+{
+    t_err.clear();
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune.clear();
     return DBSCAN_OK;
 }
 

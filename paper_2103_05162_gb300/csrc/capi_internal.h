@@ -34,8 +34,8 @@ struct Workspace {
 };
 
 struct Tuning {
-    int block;             // traversal block size (threads)
-    float cell_factor;     // DenseBox cell side factor f in (0, 1]
+    int block;             // traversal block size (threads); 0: chosen by the autotuner
+    float cell_factor;     // DenseBox cell side factor f in (0, 1]; 0: chosen by the autotuner
     // border claims (DBSCAN mode): 1 = from preprocessing's per-point
     // neighbour lists, 0 = by core points during the main traversal (no
     // per-point list; Algorithm 3 as written)
@@ -53,6 +53,31 @@ struct Tuning {
 constexpr float DEFAULT_AUTO_FRACTION_2D = 0.3f, DEFAULT_AUTO_FRACTION_3D = 0.005f;
 constexpr float DEFAULT_AUTO_OCCUPANCY = 16.0f;
 extern Tuning g_tuning;
+
+// The traversal block size and DenseBox cell factor of the run being
+// enqueued on this thread: every entry point sets it (resolve_tuning, or the
+// autotuner while it measures) before enqueueing work.
+struct RunTuning {
+    int block;
+    float cell_factor;
+};
+constexpr RunTuning DEFAULT_RUN_TUNING = {128, 1.0f};
+extern thread_local RunTuning t_run;
+// Autotuner table keys: one per kind of call (0 dbscan_run, 1 batch), dim
+// (0 for batches), ceil(log2 n), minPts (the largest, for batches),
+// algorithm, mode and ceil(log2 count) (batches).
+struct TuneKey {
+    int kind, dim, log2n, min_pts, algo, mode, log2count;
+    bool operator<(const TuneKey& o) const;
+};
+TuneKey tune_key(int kind, int dim, int64_t n, int min_pts, int algo, int mode, int64_t count);
+// the fixed knobs, or the table's entry for the key, or the defaults (never measures)
+RunTuning resolve_tuning(const TuneKey& k);
+bool autotune_on();
+bool tuned(const TuneKey& k);
+void store_tuning(const TuneKey& k, RunTuning t, float ms);
+// the candidates the autotuner measures (fixed knobs restrict them)
+int tuning_candidates(int algo, RunTuning* out, int cap);
 
 dbscan_status set_error(dbscan_status st, const char* fmt, ...);
 // empties this thread's dbscan_last_error() message (every entry point starts so)

@@ -83,6 +83,7 @@ struct dbscan_server {
     dbscan_status run_single(Workspace* w, Job* j, cudaStream_t s)
     {
         if (!w) return DBSCAN_ERR_CUDA;
+        t_run = resolve_tuning(tune_key(0, j->dim, j->n, j->min_pts, j->algo, j->mode, 0));
         dbscan_status st =
             run_pipeline(w, j->points, j->n, j->dim, j->eps, j->min_pts, j->mode, j->algo, j->labels, j->core, s);
         const dbscan_status ds = workspace_status(w, s);
@@ -109,6 +110,9 @@ struct dbscan_server {
             labels[b] = j->labels;
             cores[b] = j->core;
         }
+        int max_mp = 1;
+        for (int b = 0; b < count; ++b) max_mp = mps[b] > max_mp ? mps[b] : max_mp;
+        t_run = resolve_tuning(tune_key(1, 0, offs[count], max_mp, g[0]->algo, g[0]->mode, count));
         dbscan_status st = run_batch(w, count, offs.data(), pts.data(), dims.data(), eps.data(), mps.data(),
                                      labels.data(), cores.data(), g[0]->mode, g[0]->algo, s);
         const dbscan_status ds = workspace_status(w, s);

@@ -141,10 +141,19 @@ def test_nonfinite_input_is_rejected(algo):
     writes no label, and the next sync point reports NONFINITE; the stream
     then serves the next run normally."""
     X = blobs(1000, 3, 1)
+    # the first call of a kind runs the autotuner, which waits for the
+    # device: it reports the error itself
+    gb.tuning_clear()
+    Y = X.copy()
+    Y[3, 0] = np.inf
+    with pytest.raises(gb.DbscanError) as e:
+        gb.dbscan_run(torch.from_numpy(Y).cuda(), 0.05, 3, algo=algo)
+    assert e.value.name == "NONFINITE"
+    gb.dbscan_run(torch.from_numpy(X).cuda(), 0.05, 3, algo=algo, sync=True)  # tunes this kind
     X[17, 2] = np.nan
     pts = torch.from_numpy(X).cuda()
     labels = torch.full((1000,), -7, dtype=torch.int32, device="cuda")
-    gb.dbscan_run(pts, 0.05, 3, algo=algo, labels_out=labels)
+    gb.dbscan_run(pts, 0.05, 3, algo=algo, labels_out=labels)  # enqueued, no error yet
     with pytest.raises(gb.DbscanError) as e:
         gb.stream_status()
     assert e.value.name == "NONFINITE"
@@ -413,3 +422,55 @@ def test_claims_in_the_main_traversal_without_lists(no_border_lists, mode, algo)
     L = rs.integers(0, 12, size=(3000, 2)).astype(np.float32)
     for mp in (3, 4, 9, 40):
         check(L, 1.0, mp, mode, algo)
+
+
+# ---------------------------------------------------------------- autotuner
+
+def test_autotuner_fills_its_table_and_results_stay_exact():
+    """dbscan_set_tuning(0, 0): the first call of a kind measures the block
+    sizes and cell factors on its data and keeps the fastest; results match
+    the oracle on that call and the next, and the next call does not wait
+    for the device."""
+    gb.set_tuning(0, 0.0)
+    gb.tuning_clear()
+    n = 1 << 18
+    X = halos(n, 21, n_halos=800)
+    eps = halo_eps(n)
+    assert gb.tuning_lookup(3, n, 10) is None
+    ref = check(X, eps, 10, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX)[0]
+    entry = gb.tuning_lookup(3, n, 10)
+    assert entry is not None
+    block, f, ms = entry
+    assert block in (64, 128, 256) and f in (1.0, 0.75, 0.5) and ms > 0
+    check(X, eps, 10, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX, ref=ref)
+    assert gb.tuning_lookup(3, n, 10) == entry
+    # FDbscan: block sizes only
+    check(X, eps, 10, gb.MODE_DBSCAN, gb.ALGO_FDBSCAN, ref=ref)
+    fb = gb.tuning_lookup(3, n, 10, algo=gb.ALGO_FDBSCAN)
+    assert fb is not None and fb[1] == 1.0
+    # a fixed knob restricts the search
+    gb.set_tuning(0, 0.75)
+    gb.tuning_clear()
+    check(X, eps, 10, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX, ref=ref)
+    assert gb.tuning_lookup(3, n, 10)[1] == 0.75
+    gb.set_tuning(0, 0.0)
+
+
+def test_autotuner_for_batches():
+    from tests.test_gpu_batch_serve import _check_batch, _concat, _mixed_instances
+    gb.set_tuning(0, 0.0)
+    gb.tuning_clear()
+    inst = _mixed_instances(77)
+    flat, offs = _concat(inst)
+    pts = torch.from_numpy(flat).cuda()
+    total = int(offs[-1])
+    labels = torch.empty(total, dtype=torch.int32, device="cuda")
+    core = torch.empty(total, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        gb.dbscan_run_batch(pts, offs, [x.dim for x in inst], [x.eps for x in inst], [x.min_pts for x in inst],
+                            algo=gb.ALGO_DENSEBOX, labels_out=labels, core_out=core)
+        torch.cuda.synchronize()
+        gb.stream_status()
+        _check_batch(inst, gb.MODE_DBSCAN, gb.ALGO_DENSEBOX, labels.cpu().numpy(), core.cpu().numpy())
+    entry = gb.tuning_lookup(0, total, max(x.min_pts for x in inst), batch=True, count=len(inst))
+    assert entry is not None and entry[0] in (64, 128, 256)
