@@ -64,28 +64,60 @@ def bytes_model(n: int, d: int, m: int, key_bytes: int, packed: bool = False) ->
     }
 
 
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "preprocess_main_densebox_halos8m.md")
-TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2103_05162_gb300", "csrc", f)
-                   for f in ("traverse.cu", "internal.cuh", "build.cuh")]
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traversal_traffic_densebox_halos.json")
+STAGE_KERNELS = {"preprocess": ("k_pre", "k_list_claims"), "main": ("k_intra", "k_kinds_count", "k_kinds_write",
+                                                                     "k_main")}
 
 
 def measured_traffic(n: int, stage: str) -> float | None:
     """DRAM bytes (read + write) of one run of a traversal stage
     ("preprocess" or "main") on n points of the halo workload (DenseBox,
-    minPts 10), from the committed ncu summary, scaled by the points; None if
-    the summary is missing or the traversal sources have changed since it was
-    taken."""
-    import hashlib
-    import re
+    minPts 10), from the committed ncu summary (bytes per point of the
+    captured size, scaled by the points); None if the summary is missing or
+    the sources have changed since it was taken."""
     try:
-        text = open(TRAFFIC_SUMMARY).read()
-        per_point = float(re.search(r"^traffic_bytes_per_point_%s:\s*([0-9.]+)" % stage, text, re.M).group(1))
-        want = re.search(r"^sources_sha256:\s*([0-9a-f]{64})", text, re.M).group(1)
-        h = hashlib.sha256()
-        for f in TRAFFIC_SOURCES:
-            with open(f, "rb") as fh:
-                h.update(fh.read())
-        return per_point * n if h.hexdigest() == want else None
+        with open(TRAFFIC_JSON) as f:
+            t = json.load(f)
+        if t["sources_sha256"] != sources_sha256(COUNT_SOURCES):
+            return None
+        return t["bytes_per_point"][stage] * n
+    except Exception:
+        return None
+
+
+COUNTS_JSON = os.path.join(ROOT, "profiles", "traversal_counts_densebox_halos16m.json")
+COUNT_SOURCES = [os.path.join(ROOT, "paper_2103_05162_gb300", "csrc", f)
+                 for f in ("traverse.cu", "internal.cuh", "build.cuh", "build.cu", "capi.cu")]
+PHASES = ("lists", "preprocess", "main")
+KINDS = ("distance_tests", "box_tests", "node_visits_per_warp", "leaf_visits_per_warp")
+
+
+def sources_sha256(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def fp32_ops(d: int, dist_tests: float, box_tests: float) -> float:
+    """FP32 arithmetic of the tests (compares not counted): a distance test
+    is d subtractions, d products and d-1 sums; a point- or box-to-box test
+    is, per axis, two differences, two maxima and a product, then d-1 sums."""
+    return dist_tests * (3 * d - 1) + box_tests * (5 * d + d - 1)
+
+
+def traversal_counts(n: int) -> dict | None:
+    """Counts per point of the traversal phases on the benchmark workload,
+    from the committed counters run (None if missing, for another size, or
+    taken on other sources)."""
+    try:
+        with open(COUNTS_JSON) as f:
+            c = json.load(f)
+        if c["n"] != n or c["sources_sha256"] != sources_sha256(COUNT_SOURCES):
+            return None
+        return c
     except Exception:
         return None
 
@@ -223,6 +255,7 @@ def run_gb300(args, rank: int, world: int) -> None:
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     gb.load()
+    gb.set_tuning(args.block, args.cell_factor)
     if args.border_lists is not None:
         gb.set_border_lists(bool(args.border_lists))
     algo = gb.ALGO_DENSEBOX if args.algo == "densebox" else gb.ALGO_FDBSCAN
@@ -306,12 +339,33 @@ def run_gb300(args, rank: int, world: int) -> None:
     traffic = None
     if top in ("preprocess", "main") and algo == gb.ALGO_DENSEBOX and args.min_pts == 10:
         traffic = measured_traffic(n, top)
+        if traffic is not None:
+            traffic /= 1.0  # bytes per launch of the stage (one launch per step)
     kernels = {"preprocess": "k_pre + k_list_claims", "main": "k_intra + k_kinds_* + k_main x3"}
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kernels.get(top, top), "stage": top,
-                "peak_source": peak_kind, "algorithmic_bytes_per_launch": model[top], "launch_ms": stage_ms[top],
-                "traffic_source": "profiles/preprocess_main_densebox_halos8m.md (8M capture scaled by points)"
-                if traffic is not None else None}
+    counts = traversal_counts(n) if (algo == gb.ALGO_DENSEBOX and args.min_pts == 10) else None
+    stage_frac_hbm = {k: model[k] / (stage_ms[k] / 1e3) / 1e9 / peak for k in stage_ms}
+    if top in ("preprocess", "main") and counts is not None:
+        # the traversals are bound by instruction issue of fp32 / integer
+        # work, not by DRAM: their roofline is the fp32 ALU rate, SMs x 128
+        # lanes x the SM clock under load (one non-fused fp32 operation per
+        # lane per cycle)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        peak_alu = sms * 128 * mhz * 1e6 / 1e12
+        per_pt = counts["per_point"][top]
+        ops = fp32_ops(d, per_pt["distance_tests"], per_pt["box_tests"]) * n
+        achieved_alu = ops / (stage_ms[top] / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved_alu, "peak": peak_alu, "unit": "TFLOP/s",
+                    "frac": achieved_alu / peak_alu, "traffic": traffic, "kernel": kernels.get(top, top),
+                    "stage": top, "peak_source": f"derived: {sms} SMs x 128 fp32 lanes x {mhz:.0f} MHz (sampled)",
+                    "fp32_ops_per_launch": ops, "launch_ms": stage_ms[top],
+                    "tests_per_point": per_pt, "counts_source": os.path.relpath(COUNTS_JSON, ROOT),
+                    "hbm_frac": stage_frac_hbm[top]}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "kernel": kernels.get(top, top), "stage": top,
+                    "peak_source": peak_kind, "algorithmic_bytes_per_launch": model[top],
+                    "launch_ms": stage_ms[top]}
 
     small = small_job_figures(args, dev) if (rank == 0 and not args.no_small_jobs) else {}
 
@@ -340,12 +394,107 @@ def run_gb300(args, rank: int, world: int) -> None:
             "clocks": clocks,
             "gpu_launches": int(launches),
             "stages_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stages_hbm_frac": {k: round(v, 4) for k, v in stage_frac_hbm.items()},
             "hbm_frac_path": path_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
             "features_per_s": value * d,
             "stats": stats,
             **small,
         }
         print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ measurement modes
+def run_counters_mode(args) -> None:
+    """Counts the traversal's tests on the benchmark workload with the
+    counters build of the library (libgbdbscan_counters.so, -DGBD_COUNTERS)
+    and writes them per point to profiles/ (the default line reads them for
+    its ALU roofline). Timing is meaningless in that build and is not taken."""
+    import ctypes
+
+    import torch
+
+    from paper_2103_05162_gb300 import _build
+
+    lib = ctypes.CDLL(_build.build(counters=True))
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    lib.dbscan_run.argtypes = [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp]
+    lib.dbscan_traversal_counters.argtypes = [vp, i32]
+    lib.dbscan_set_tuning.argtypes = [i32, f32]
+    lib.dbscan_last_stats.argtypes = [vp, vp]
+    lib.dbscan_stream_status.argtypes = [vp]
+    for f in (lib.dbscan_run, lib.dbscan_traversal_counters, lib.dbscan_set_tuning, lib.dbscan_last_stats,
+              lib.dbscan_stream_status):
+        f.restype = i32
+    assert lib.dbscan_set_tuning(128, 1.0) == 0  # the autotuner's choice for this workload; no tuning runs
+    algo = 1 if args.algo == "densebox" else 0
+    X, eps = workload(args.n, args.seed)
+    n, d = X.shape
+    pts = torch.from_numpy(X).cuda()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = (ctypes.c_uint64 * 12)()
+
+    def run():
+        assert lib.dbscan_run(ctypes.c_void_p(pts.data_ptr()), n, d, eps, args.min_pts, 0, algo,
+                              ctypes.c_void_p(labels.data_ptr()), None, stream) == 0
+        assert lib.dbscan_stream_status(stream) == 0
+
+    run()
+    assert lib.dbscan_traversal_counters(out, 12) == 0  # discard the first run's
+    run()
+    assert lib.dbscan_traversal_counters(out, 12) == 0
+    st = (ctypes.c_int64 * 2)()
+    lib.dbscan_last_stats(stream, st)
+    per_point = {ph: {k: out[4 * i + j] / n for j, k in enumerate(KINDS)} for i, ph in enumerate(PHASES)}
+    rec = {
+        "what": "traversal tests per point, one dbscan_run (counters build; the product build counts nothing)",
+        "workload": workload_desc(n, eps, args.min_pts), "n": n, "dim": d, "min_pts": args.min_pts,
+        "algo": args.algo, "leaves": int(st[0]), "dense_cells": int(st[1]),
+        "per_point": per_point, "totals": {ph: {k: int(out[4 * i + j]) for j, k in enumerate(KINDS)}
+                                             for i, ph in enumerate(PHASES)},
+        "fp32_ops_per_test": {"distance": 3 * d - 1, "box": 6 * d - 1},
+        "sources_sha256": sources_sha256(COUNT_SOURCES),
+        "command": f"python bench.py --mode counters --n {args.n} --min-pts {args.min_pts} --algo {args.algo}",
+    }
+    if args.n == 1 << 24 and args.min_pts == 10 and args.algo == "densebox":
+        with open(COUNTS_JSON, "w") as f:
+            json.dump(rec, f, indent=1)
+    print(json.dumps(rec), flush=True)
+
+
+def run_traffic_mode(args) -> None:
+    """Per-point DRAM bytes of the traversal stages from an ncu launch CSV
+    (metrics dram__bytes_read.sum, dram__bytes_write.sum; one run of the
+    halo workload at --n points after warm-up), written to profiles/ with the
+    capture size, the sources' hash and the scaling rule."""
+    import csv
+    rows = list(csv.reader(open(args.ncu_csv)))
+    hdr_i = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hdr_i]
+    kcol, mcol, ucol, vcol = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value"))
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per_kernel = {}
+    for r in rows[hdr_i + 1:]:
+        if len(r) <= vcol or not r[mcol].startswith("dram__bytes"):
+            continue
+        name = r[kcol].split("(")[0].split("<")[0].split("::")[-1].split()[-1]
+        per_kernel[name] = per_kernel.get(name, 0.0) + float(r[vcol].replace(",", "")) * scale[r[ucol]]
+    runs = args.traffic_runs
+    by_stage = {st: sum(v for k, v in per_kernel.items() if k in ks) / runs for st, ks in STAGE_KERNELS.items()}
+    rec = {
+        "what": "DRAM bytes (read + write) per point of the traversal stages, ncu dram__bytes_read.sum + "
+                "dram__bytes_write.sum over their kernels, per run",
+        "capture_n": args.n, "runs_captured": runs,
+        "bytes_per_point": {st: v / args.n for st, v in by_stage.items()},
+        "kernels_bytes_per_run": {k: v / runs for k, v in per_kernel.items()},
+        "scaling": "bytes of a run at n points = bytes_per_point x n (same workload family, halos shrunk in "
+                   "proportion below 2^24 points)",
+        "sources_sha256": sources_sha256(COUNT_SOURCES),
+        "command": args.ncu_command,
+    }
+    with open(TRAFFIC_JSON, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec), flush=True)
 
 
 # ------------------------------------------------------------ batch and serve
@@ -745,10 +894,16 @@ def main():
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-small-jobs", action="store_true", help="skip the batched / served small-job figures")
+    ap.add_argument("--block", type=int, default=0, help="traversal block size (0: autotuner)")
+    ap.add_argument("--cell-factor", type=float, default=0.0, help="DenseBox cell factor (0: autotuner)")
     ap.add_argument("--border-lists", type=int, choices=[0, 1], default=None,
                     help="border claims from per-point neighbour lists (1) or in the main traversal (0); "
                          "default: the library's default")
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep", "slabs"], default="step",
+    ap.add_argument("--ncu-csv", default=None, help="--mode traffic: the ncu launch CSV to summarise")
+    ap.add_argument("--ncu-command", default="", help="--mode traffic: the command that produced the CSV")
+    ap.add_argument("--traffic-runs", type=int, default=1, help="--mode traffic: clustering runs captured")
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep", "slabs", "counters", "traffic"],
+                    default="step",
                     help="step: the headline line (default); batch: fused batch vs per-instance runs; "
                          "serve: Poisson-arrival serving vs sequential runs; sweep: several minPts over one "
                          "index vs one run each; slabs: slab-wise clustering from host memory "
@@ -777,7 +932,7 @@ def main():
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
             {"batch": run_batch_mode, "serve": run_serve_mode, "sweep": run_sweep_mode,
-             "slabs": run_slabs_mode}[args.mode](args)
+             "slabs": run_slabs_mode, "counters": run_counters_mode, "traffic": run_traffic_mode}[args.mode](args)
         return
     if world > 1:
         import torch

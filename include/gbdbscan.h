@@ -330,6 +330,16 @@ const char* dbscan_profile_stage_name(int stage);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 int64_t dbscan_kernel_launches(void);
 
+/* Traversal counters, for measurement (the paper has no counterpart). Only a
+ * library built with -DGBD_COUNTERS counts (the product build returns
+ * DBSCAN_ERR_NOT_FOUND). Waits for the device, writes out[phase * 4 + kind]
+ * summed since the last call and zeroes them: phase 0 = per-leaf index
+ * lists, 1 = preprocessing, 2 = main phase (intra-tile and traversal);
+ * kind 0 = point-to-point distance tests (per lane), 1 = point- and
+ * box-to-box tests (per lane), 2 = node visits and 3 = leaf visits (per
+ * warp). cap >= 12. */
+dbscan_status dbscan_traversal_counters(uint64_t* out, int cap);
+
 /* Test hooks of the radix sort's bounded look-back wait (the paper has no
  * counterpart; they exist to exercise the timeout path without a fault):
  * every later sort waits at most wait_limit polls (negative: the default,

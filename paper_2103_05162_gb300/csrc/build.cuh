@@ -262,5 +262,8 @@ cudaError_t launch_cluster_from_counts(const ClusterArgs& a, int min_pts, cudaSt
 cudaError_t launch_cluster_core_from_input(const ClusterArgs& a, const uint8_t* core_in, cudaStream_t s);
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint8_t* core_out, cudaStream_t s);
+// traversal counters (built with -DGBD_COUNTERS only)
+bool counters_built();
+cudaError_t counters_take(uint64_t* out);  // CNT_PHASES * CNT_KINDS values
 
 }  // namespace gbd

@@ -1103,6 +1103,16 @@ dbscan_status dbscan_last_choice(dbscan_stream stream, int* algo_out, float* est
     return DBSCAN_OK;
 }
 
+dbscan_status dbscan_traversal_counters(uint64_t* out, int cap)
+{
+    t_err.clear();
+    if (!out || cap < CNT_PHASES * CNT_KINDS) return set_error(DBSCAN_ERR_INVALID_ARG, "need 12 output words");
+    if (!counters_built())
+        return set_error(DBSCAN_ERR_NOT_FOUND, "this library was built without traversal counters (GBD_COUNTERS)");
+    TRY_CUDA(counters_take(out));
+    return DBSCAN_OK;
+}
+
 dbscan_status dbscan_test_sort_hooks(int64_t wait_limit, int stall_first_tile)
 {
     t_err.clear();

@@ -22,6 +22,29 @@ constexpr unsigned ERR_NONFINITE = 4u;     // the input holds a NaN or an infini
 constexpr int SPIN_LIMIT = 1 << 22;
 
 // ---------------------------------------------------------------------------
+// Traversal counters (an opt-in build, -DGBD_COUNTERS; the product build
+// compiles every GBD_COUNT to nothing): point-to-point distance tests,
+// point- and box-to-box tests, node visits and leaf visits (both per warp),
+// per phase (0 index lists, 1 preprocessing, 2 main phase), summed over the
+// lanes that take part with one atomic per warp.
+// ---------------------------------------------------------------------------
+enum { CNT_DIST = 0, CNT_BOX = 1, CNT_NODE = 2, CNT_LEAF = 3, CNT_KINDS = 4, CNT_PHASES = 3 };
+#ifdef GBD_COUNTERS
+static __device__ unsigned long long g_counts[CNT_PHASES * CNT_KINDS];
+static __device__ int g_count_phase;
+__device__ __forceinline__ void gbd_count(int kind, unsigned v)
+{
+    const unsigned m = __activemask();
+    const unsigned t = __reduce_add_sync(m, v);
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && t)
+        atomicAdd(&g_counts[g_count_phase * CNT_KINDS + kind], (unsigned long long)t);
+}
+#define GBD_COUNT(kind, v) gbd_count((kind), (unsigned)(v))
+#else
+#define GBD_COUNT(kind, v) ((void)0)
+#endif
+
+// ---------------------------------------------------------------------------
 // The distance test, fixed as the fp32 squared form with no fused multiply-add
 // (explicit round-to-nearest intrinsics, which the compiler never contracts):
 //   dk = fl(x_k - y_k); s = fl(d0*d0); s = fl(s + fl(dk*dk)); adjacent <=> s <= fl(eps*eps)
@@ -32,6 +55,7 @@ __device__ __forceinline__ float sqr_rn(float a) { return __fmul_rn(a, a); }
 
 __device__ __forceinline__ float dist2(const float4& a, const float4& b)
 {
+    GBD_COUNT(CNT_DIST, 1);
     float s = sqr_rn(__fsub_rn(a.x, b.x));
     s = __fadd_rn(s, sqr_rn(__fsub_rn(a.y, b.y)));
     s = __fadd_rn(s, sqr_rn(__fsub_rn(a.z, b.z)));
@@ -40,6 +64,7 @@ __device__ __forceinline__ float dist2(const float4& a, const float4& b)
 
 __device__ __forceinline__ float dist2(const float2& a, const float2& b)
 {
+    GBD_COUNT(CNT_DIST, 1);
     float s = sqr_rn(__fsub_rn(a.x, b.x));
     s = __fadd_rn(s, sqr_rn(__fsub_rn(a.y, b.y)));
     return s;
@@ -79,6 +104,7 @@ __device__ __forceinline__ void st_cg(PtN<D>* p, const PtN<D>& v)
 template <int D>
 __device__ __forceinline__ float dist2(const PtN<D>& a, const PtN<D>& b)
 {
+    GBD_COUNT(CNT_DIST, 1);
     float s = sqr_rn(__fsub_rn(a.c[0], b.c[0]));
 #pragma unroll
     for (int k = 1; k < D; ++k) s = __fadd_rn(s, sqr_rn(__fsub_rn(a.c[k], b.c[k])));

@@ -74,6 +74,7 @@ template <int D> struct NB {
     }
     __device__ static __forceinline__ void pd2(const typename T::Node& n, const PP& p, float& dl, float& dr)
     {
+        GBD_COUNT(CNT_BOX, 2);
         f32x2 s = sqr2(gap_rn2(pk2(n.ax[0].x, n.ax[0].y), pk2(n.ax[0].z, n.ax[0].w), p.c[0]));
 #pragma unroll
         for (int k = 1; k < D; ++k)
@@ -83,6 +84,7 @@ template <int D> struct NB {
     __device__ static __forceinline__ void bd2(const typename T::Node& n, const typename T::Box& q, float& dl,
                                                float& dr)
     {
+        GBD_COUNT(CNT_BOX, 2);
         f32x2 s = sqr2(gap2_rn2(pk2(q.lo.c[0], q.lo.c[0]), pk2(q.hi.c[0], q.hi.c[0]), pk2(n.ax[0].x, n.ax[0].y),
                                 pk2(n.ax[0].z, n.ax[0].w)));
 #pragma unroll
@@ -93,10 +95,12 @@ template <int D> struct NB {
     }
     __device__ static __forceinline__ float pbox(const typename T::Point& p, const typename T::Box& b)
     {
+        GBD_COUNT(CNT_BOX, 1);
         return T::box_dist2(p, b);
     }
     __device__ static __forceinline__ float bbox(const typename T::Box& q, const typename T::Box& b)
     {
+        GBD_COUNT(CNT_BOX, 1);
         return T::box_box_dist2(q, b);
     }
     __device__ static __forceinline__ typename T::Point shfl(const typename T::Point& p, int src)
@@ -128,6 +132,7 @@ template <> struct NB<3> {
     // squared point-to-box distances of both children (box_dist2's order)
     __device__ static __forceinline__ void pd2(const T::Node& n, const PP& p, float& dl, float& dr)
     {
+        GBD_COUNT(CNT_BOX, 2);
         f32x2 s = sqr2(gap_rn2(pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w), p.x));
         s = add2(s, sqr2(gap_rn2(pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w), p.y)));
         s = add2(s, sqr2(gap_rn2(pk2(n.c.x, n.c.y), pk2(n.c.z, n.c.w), p.z)));
@@ -136,6 +141,7 @@ template <> struct NB<3> {
     // squared box-to-box distances of both children from q (box_box_dist2's order)
     __device__ static __forceinline__ void bd2(const T::Node& n, const T::Box& q, float& dl, float& dr)
     {
+        GBD_COUNT(CNT_BOX, 2);
         f32x2 s = sqr2(gap2_rn2(pk2(q.lo.x, q.lo.x), pk2(q.hi.x, q.hi.x), pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w)));
         s = add2(s, sqr2(gap2_rn2(pk2(q.lo.y, q.lo.y), pk2(q.hi.y, q.hi.y), pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w))));
         s = add2(s, sqr2(gap2_rn2(pk2(q.lo.z, q.lo.z), pk2(q.hi.z, q.hi.z), pk2(n.c.x, n.c.y), pk2(n.c.z, n.c.w))));
@@ -143,10 +149,12 @@ template <> struct NB<3> {
     }
     __device__ static __forceinline__ float pbox(const T::Point& p, const T::Box& b)
     {
+        GBD_COUNT(CNT_BOX, 1);
         return T::box_dist2(p, b.lo.x, b.lo.y, b.lo.z, b.hi.x, b.hi.y, b.hi.z);
     }
     __device__ static __forceinline__ float bbox(const T::Box& q, const T::Box& b)
     {
+        GBD_COUNT(CNT_BOX, 1);
         return T::box_box_dist2(q, b.lo.x, b.lo.y, b.lo.z, b.hi.x, b.hi.y, b.hi.z);
     }
     __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
@@ -174,22 +182,26 @@ template <> struct NB<2> {
     }
     __device__ static __forceinline__ void pd2(const T::Node& n, const PP& p, float& dl, float& dr)
     {
+        GBD_COUNT(CNT_BOX, 2);
         f32x2 s = sqr2(gap_rn2(pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w), p.x));
         s = add2(s, sqr2(gap_rn2(pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w), p.y)));
         unpk2(s, dl, dr);
     }
     __device__ static __forceinline__ void bd2(const T::Node& n, const T::Box& q, float& dl, float& dr)
     {
+        GBD_COUNT(CNT_BOX, 2);
         f32x2 s = sqr2(gap2_rn2(pk2(q.lo.x, q.lo.x), pk2(q.hi.x, q.hi.x), pk2(n.a.x, n.a.y), pk2(n.a.z, n.a.w)));
         s = add2(s, sqr2(gap2_rn2(pk2(q.lo.y, q.lo.y), pk2(q.hi.y, q.hi.y), pk2(n.b.x, n.b.y), pk2(n.b.z, n.b.w))));
         unpk2(s, dl, dr);
     }
     __device__ static __forceinline__ float pbox(const T::Point& p, const T::Box& b)
     {
+        GBD_COUNT(CNT_BOX, 1);
         return T::box_dist2(p, b.lo.x, b.lo.y, b.hi.x, b.hi.y);
     }
     __device__ static __forceinline__ float bbox(const T::Box& q, const T::Box& b)
     {
+        GBD_COUNT(CNT_BOX, 1);
         return T::box_box_dist2(q, b.lo.x, b.lo.y, b.hi.x, b.hi.y);
     }
     __device__ static __forceinline__ T::Point shfl(const T::Point& p, int src)
@@ -209,6 +221,7 @@ template <int D> struct __align__(16) SoA {
     }
     __device__ __forceinline__ void d2pair(const typename NB<D>::PP& p, int u, float& d0, float& d1) const
     {
+        GBD_COUNT(CNT_DIST, 2);
         f32x2 s = sqr2(sub2(p.c[0], *reinterpret_cast<const f32x2*>(&c[0][u])));
 #pragma unroll
         for (int k = 1; k < D; ++k) s = add2(s, sqr2(sub2(p.c[k], *reinterpret_cast<const f32x2*>(&c[k][u]))));
@@ -216,6 +229,7 @@ template <int D> struct __align__(16) SoA {
     }
     __device__ __forceinline__ float d2(const typename Traits<D>::Point& p, int u) const
     {
+        GBD_COUNT(CNT_DIST, 1);
         float s = sqr_rn(__fsub_rn(p.c[0], c[0][u]));
 #pragma unroll
         for (int k = 1; k < D; ++k) s = __fadd_rn(s, sqr_rn(__fsub_rn(p.c[k], c[k][u])));
@@ -228,6 +242,7 @@ template <> struct __align__(16) SoA<3> {
     // dist2(p, point u) and dist2(p, point u + 1) for even u (p packed)
     __device__ __forceinline__ void d2pair(const NB<3>::PP& p, int u, float& d0, float& d1) const
     {
+        GBD_COUNT(CNT_DIST, 2);
         const f32x2 bx = *reinterpret_cast<const f32x2*>(&x[u]);
         const f32x2 by = *reinterpret_cast<const f32x2*>(&y[u]);
         const f32x2 bz = *reinterpret_cast<const f32x2*>(&z[u]);
@@ -243,6 +258,7 @@ template <> struct __align__(16) SoA<2> {
     __device__ __forceinline__ void put(int l, const float2& p) { x[l] = p.x; y[l] = p.y; }
     __device__ __forceinline__ void d2pair(const NB<2>::PP& p, int u, float& d0, float& d1) const
     {
+        GBD_COUNT(CNT_DIST, 2);
         const f32x2 bx = *reinterpret_cast<const f32x2*>(&x[u]);
         const f32x2 by = *reinterpret_cast<const f32x2*>(&y[u]);
         f32x2 s = sqr2(sub2(p.x, bx));
@@ -279,6 +295,7 @@ __device__ __forceinline__ void traverse_loop(const typename Traits<D>::Node* __
             return;
         }
         const auto nd = NB<D>::load(nodes, node);
+        GBD_COUNT(CNT_NODE, lane == 0);
         bool hl, hr;
         v.hits(nd, hl, hr);
         const unsigned ml = nd.m.z >= v.mask_lo ? __ballot_sync(FULL, hl) : 0u;
@@ -292,6 +309,7 @@ __device__ __forceinline__ void traverse_loop(const typename Traits<D>::Node* __
             if (!mk) continue;
             const int child = c ? nd.m.y : nd.m.x;
             if (child >= leaf0) {
+                GBD_COUNT(CNT_LEAF, lane == 0);
                 if (v.leaf(child - leaf0, mk, c ? NB<D>::box_r(nd) : NB<D>::box_l(nd))) return;
             } else if (next < 0) {
                 next = child;
@@ -354,6 +372,7 @@ __device__ __forceinline__ void traverse_roots(const typename Traits<D>::Node* _
             b.lo = nodebox[r.x].lo;
             b.hi = nodebox[r.x].hi;
             const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+            GBD_COUNT(CNT_LEAF, lane == 0 && mk);
             if (mk && v.leaf(r.x - leaf0, mk, b)) return;
         } else {
             if (lane == 0) stack[sp] = r.x;
@@ -1094,6 +1113,7 @@ __device__ __forceinline__ void walk(const DevArgs<D>& a, int64_t m, V& v, int* 
                 b.lo = a.nodebox[leaf0 + U].lo;
                 b.hi = a.nodebox[leaf0 + U].hi;
                 const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+                GBD_COUNT(CNT_LEAF, lane == 0 && mk);
                 if (mk && v.leaf(U, mk, b)) return;
             }
         } else {
@@ -1127,6 +1147,7 @@ __device__ __forceinline__ void walk(const DevArgs<D>& a, int64_t m, V& v, int* 
                     b.lo = a.nodebox[leaf0 + Us].lo;
                     b.hi = a.nodebox[leaf0 + Us].hi;
                     const unsigned mk = __ballot_sync(FULL, v.hit_box(b));
+                    GBD_COUNT(CNT_LEAF, lane == 0 && mk);
                     if (mk && v.leaf_rec(Us, mk, b, rs, ss)) return;
                 }
             }
@@ -1525,6 +1546,21 @@ __global__ void k_relabel(const int32_t* labels, const uint8_t* __restrict__ cor
     }
 }
 
+#ifdef GBD_COUNTERS
+__global__ void k_count_phase(int phase) { g_count_phase = phase; }
+#endif
+
+// the traversal counters' phase for the kernels that follow (counters build)
+void count_phase(int phase, cudaStream_t s)
+{
+#ifdef GBD_COUNTERS
+    k_count_phase<<<1, 1, 0, s>>>(phase);
+#else
+    (void)phase;
+    (void)s;
+#endif
+}
+
 // blocks of a persistent launch: as many as fit on all SMs at once
 int persistent_blocks(const void* kernel, int block, size_t smem)
 {
@@ -1638,6 +1674,7 @@ cudaError_t launch_cluster_from_counts(const ClusterArgs& a, int min_pts, cudaSt
 
 cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
 {
+    count_phase(0, s);
     int64_t gm = (a.m_cap + 255) / 256;
     if (gm > 152 * 8) gm = 152 * 8;
 #define TS_LAUNCH(D) k_tile_start<D><<<(unsigned)gm, 256, 0, s>>>(dev_args<D>(a), a.parent, a.nmeta)
@@ -1658,6 +1695,7 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
     // Algorithm 3: no preprocessing for minPts <= 2 (counts for several minPts
     // are always taken)
     if (a.min_pts <= 2 && !a.ncount) return cudaSuccess;
+    count_phase(1, s);
     cudaError_t e;
     // points that keep no list (instances of a batch with minPts <= 2) read 0
     if (a.lcap > 0 && (e = cudaMemsetAsync(a.nbr, 0, (size_t)a.n, s)) != cudaSuccess) return e;
@@ -1676,6 +1714,7 @@ cudaError_t launch_cluster_pre(const ClusterArgs& a, cudaStream_t s)
 
 cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
 {
+    count_phase(2, s);
 #define MAIN_RUN(D) run_main<D>(a, s)
     GBD_DIM_SWITCH(a.dim, MAIN_RUN)
 #undef MAIN_RUN
@@ -1701,6 +1740,32 @@ cudaError_t launch_cluster_final(const ClusterArgs& a, int32_t* labels_out, uint
                                            a.ctrl);
     note_launches(2);
     return cudaGetLastError();
+}
+
+bool counters_built()
+{
+#ifdef GBD_COUNTERS
+    return true;
+#else
+    return false;
+#endif
+}
+
+// the traversal counters since the last read ([phase][kind]), then zeroed
+cudaError_t counters_take(uint64_t* out)
+{
+#ifdef GBD_COUNTERS
+    unsigned long long h[CNT_PHASES * CNT_KINDS] = {};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(h, g_counts, sizeof(h));
+    for (int i = 0; i < CNT_PHASES * CNT_KINDS; ++i) out[i] = h[i];
+    const unsigned long long z[CNT_PHASES * CNT_KINDS] = {};
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_counts, z, sizeof(z));
+    return e;
+#else
+    for (int i = 0; i < CNT_PHASES * CNT_KINDS; ++i) out[i] = 0;
+    return cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace gbd

@@ -87,27 +87,80 @@ def _load_bench():
     return mod
 
 
-def test_measured_traffic_per_stage_and_source_check(tmp_path):
-    """The roofline's traffic comes from a profile summary per stage, scaled
-    by the points, and only while the sources still hash to the recorded
-    value."""
+def _fake_sources(b, tmp_path):
     import hashlib
-    b = _load_bench()
     srcs = []
     for i, text in enumerate((b"kernel one\n", b"kernel two\n")):
         f = tmp_path / f"src{i}.cu"
         f.write_bytes(text)
         srcs.append(str(f))
-    digest = hashlib.sha256(b"kernel one\nkernel two\n").hexdigest()
-    summary = tmp_path / "summary.md"
-    summary.write_text("# capture\n\ntraffic_bytes_per_point_preprocess: 45.5\n"
-                       "traffic_bytes_per_point_main: 22.25\nsources_sha256: %s\n" % digest)
-    b.TRAFFIC_SUMMARY, b.TRAFFIC_SOURCES = str(summary), srcs
+    b.COUNT_SOURCES = srcs
+    return hashlib.sha256(b"kernel one\nkernel two\n").hexdigest()
+
+
+def test_measured_traffic_per_stage_and_source_check(tmp_path):
+    """The roofline's traffic comes from the ncu summary in profiles/ (JSON:
+    bytes per point per stage), scaled by the points, and only while the
+    sources still hash to the recorded value."""
+    b = _load_bench()
+    digest = _fake_sources(b, tmp_path)
+    summary = tmp_path / "traffic.json"
+    summary.write_text(json.dumps({"bytes_per_point": {"preprocess": 45.5, "main": 22.25},
+                                   "sources_sha256": digest, "capture_n": 8388608}))
+    b.TRAFFIC_JSON = str(summary)
     assert b.measured_traffic(1000, "preprocess") == pytest.approx(45500.0)
     assert b.measured_traffic(2000, "main") == pytest.approx(44500.0)
     assert b.measured_traffic(1000, "sort") is None          # no figure for that stage
     (tmp_path / "src1.cu").write_bytes(b"kernel two, changed\n")
     assert b.measured_traffic(1000, "preprocess") is None    # sources changed since the capture
+
+
+def test_traversal_counts_are_used_only_for_their_workload_and_sources(tmp_path):
+    b = _load_bench()
+    digest = _fake_sources(b, tmp_path)
+    rec = {"n": 1 << 24, "sources_sha256": digest,
+           "per_point": {"preprocess": {"distance_tests": 40.0, "box_tests": 12.0}}}
+    f = tmp_path / "counts.json"
+    f.write_text(json.dumps(rec))
+    b.COUNTS_JSON = str(f)
+    assert b.traversal_counts(1 << 24)["per_point"]["preprocess"]["distance_tests"] == 40.0
+    assert b.traversal_counts(1 << 20) is None
+    (tmp_path / "src0.cu").write_bytes(b"other\n")
+    assert b.traversal_counts(1 << 24) is None
+
+
+def test_fp32_operations_per_test():
+    """3D: a distance test is 3 differences, 3 products and 2 sums; a box
+    test 3 x (2 differences, 2 maxima, 1 product) + 2 sums."""
+    b = _load_bench()
+    assert b.fp32_ops(3, 1, 0) == 8 and b.fp32_ops(3, 0, 1) == 17
+    assert b.fp32_ops(2, 1, 0) == 5 and b.fp32_ops(2, 0, 1) == 11
+
+
+def test_traffic_summary_from_an_ncu_csv(tmp_path):
+    """--mode traffic sums dram bytes of each stage's kernels from the
+    launch CSV (units converted) and divides by the runs and points."""
+    b = _load_bench()
+    _fake_sources(b, tmp_path)
+    csv_path = tmp_path / "launches.csv"
+    lines = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    for k, unit, rd, wr in (("void k_pre<3>(DevArgs<T1>)", "Mbyte", "2.5", "0.5"),
+                            ("k_list_claims(const int *)", "Kbyte", "500", "500"),
+                            ("void k_main<3, 1>(DevArgs<T1>)", "Mbyte", "1", "1"),
+                            ("void k_intra<3>(DevArgs<T1>)", "byte", "1000000", "0"),
+                            ("k_onesweep", "Mbyte", "9", "9")):
+        lines.append(f'"1","{k}","dram__bytes_read.sum","{unit}","{rd}"')
+        lines.append(f'"1","{k}","dram__bytes_write.sum","{unit}","{wr}"')
+    csv_path.write_text("\n".join(lines) + "\n")
+    out = tmp_path / "traffic.json"
+    b.TRAFFIC_JSON = str(out)
+
+    class A:
+        ncu_csv, n, traffic_runs, ncu_command = str(csv_path), 1000, 1, "ncu ..."
+    b.run_traffic_mode(A)
+    rec = json.loads(out.read_text())
+    assert rec["bytes_per_point"]["preprocess"] == pytest.approx(4e6 / 1000)
+    assert rec["bytes_per_point"]["main"] == pytest.approx(3e6 / 1000)
 
 
 def test_bytes_model_packed_sort_moves_a_third_less():
