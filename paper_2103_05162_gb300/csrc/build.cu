@@ -580,8 +580,11 @@ __global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t
 }
 
 // ---------------------------------------------------------------------------
-// Leaf boxes: exact min/max of each leaf's points (one warp per leaf), stored
-// at unified index (m-1) + l of the node-box array.
+// Leaf boxes: exact min/max of each leaf's points, stored at unified index
+// (m-1) + l of the node-box array. A thread takes a leaf of at most TILE
+// points (reading its contiguous points in turn: few instructions per point,
+// and consecutive threads' ranges share cache lines); the leaves larger than
+// that (dense cells) are taken afterwards by the whole warp, one at a time.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, const int2* __restrict__ leafr,
@@ -590,16 +593,32 @@ __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, c
     using T = Traits<D>;
     const int lane = threadIdx.x & 31;
     const int64_t m = ctrl[CTRL_M];
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t l = wid; l < m; l += nw) {
-        const int2 r = leafr[l];
-        const int s = r.x, e = r.y & 0x7fffffff;
-        typename T::Box b = T::empty_box();
-        for (int j = s + lane; j < e; j += 32) T::grow(b, sp[j]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < m; base += stride) {
+        const int64_t l = base + lane;
+        int s = 0, e = 0;
+        if (l < m) {
+            const int2 r = leafr[l];
+            s = r.x;
+            e = r.y & 0x7fffffff;
+        }
+        const bool small = l < m && e - s <= TILE;
+        if (small) {
+            typename T::Box b = T::empty_box();
+            for (int j = s; j < e; ++j) T::grow(b, sp[j]);
+            nodebox[(m - 1) + l] = b;
+        }
+        unsigned big = __ballot_sync(FULL, l < m && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int bs = __shfl_sync(FULL, s, src), be = __shfl_sync(FULL, e, src);
+            typename T::Box b = T::empty_box();
+            for (int j = bs + lane; j < be; j += 32) T::grow(b, sp[j]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
-        if (lane == 0) nodebox[(m - 1) + l] = b;
+            for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
+            if (lane == 0) nodebox[(m - 1) + base + src] = b;
+        }
     }
 }
 
@@ -882,10 +901,9 @@ void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lke
                  int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
                  int2* range_out)
 {
-    const unsigned gw = grid_for(m_cap * 32, 256, 152 * 16);
     const unsigned g = grid_for(m_cap, 256, 152 * 16);
 #define LB_LAUNCH(D)                                                                                         \
-    k_leaf_boxes<D><<<gw, 256, 0, s>>>(static_cast<const typename Traits<D>::Point*>(sp), leafr, ctrl,         \
+    k_leaf_boxes<D><<<g, 256, 0, s>>>(static_cast<const typename Traits<D>::Point*>(sp), leafr, ctrl,         \
                                        static_cast<typename Traits<D>::Box*>(nodebox))
     GBD_DIM_SWITCH(dim, LB_LAUNCH)
 #undef LB_LAUNCH
