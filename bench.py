@@ -497,6 +497,58 @@ def run_traffic_mode(args) -> None:
     print(json.dumps(rec), flush=True)
 
 
+def run_tune_mode(args) -> None:
+    """The autotuner's choice on each workload of the measurement plan: the
+    table is cleared, the first call of the kind measures the candidates,
+    and the steady-state time per call (CUDA events, 5 runs after 2) is taken
+    with the tuned knobs and with the fixed defaults (block 128, f = 1)."""
+    import torch
+
+    import paper_2103_05162_gb300 as gb
+    from workloads import blobs, halo_eps, halos, roads
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    cases = [("blobs 16K 3D", blobs(16384, 3, 0), 0.03, 5, "densebox"),
+             ("blobs 16K 3D", blobs(16384, 3, 0), 0.03, 5, "fdbscan"),
+             ("roads 4M 2D", roads(1 << 22, 1), 2e-4, 10, "fdbscan"),
+             ("roads 4M 2D", roads(1 << 22, 1), 2e-4, 10, "densebox")]
+    H = halos(1 << 24, 2)
+    for mp in (10, 2):
+        for al in ("densebox", "fdbscan"):
+            cases.append(("halos 16M 3D", H, halo_eps(1 << 24), mp, al))
+    rows = []
+    for name, X, eps, mp, al in cases:
+        pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        lab = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+        gb.set_tuning(0, 0.0)
+        gb.tuning_clear()
+        t = time.perf_counter()
+        gb.dbscan_run(pts, eps, mp, algo=al, labels_out=lab)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t
+        entry = gb.tuning_lookup(X.shape[1], X.shape[0], mp, algo=al)
+        ms_tuned = timed(lambda: gb.dbscan_run(pts, eps, mp, algo=al, labels_out=lab))
+        gb.set_tuning(128, 1.0)
+        ms_fixed = timed(lambda: gb.dbscan_run(pts, eps, mp, algo=al, labels_out=lab))
+        gb.set_tuning(0, 0.0)
+        gb.stream_status()
+        rows.append({"workload": name, "n": X.shape[0], "dim": X.shape[1], "min_pts": mp, "algo": al,
+                     "block": entry[0], "cell_factor": entry[1], "tuning_call_s": round(tune_s, 3),
+                     "ms_tuned": round(ms_tuned, 4), "ms_fixed_128_f1": round(ms_fixed, 4)})
+        print(json.dumps(rows[-1]), flush=True)
+
+
 # ------------------------------------------------------------ batch and serve
 SMALL_BATCH = 512
 SMALL_SERVE_JOBS = 400
@@ -902,7 +954,7 @@ def main():
     ap.add_argument("--ncu-csv", default=None, help="--mode traffic: the ncu launch CSV to summarise")
     ap.add_argument("--ncu-command", default="", help="--mode traffic: the command that produced the CSV")
     ap.add_argument("--traffic-runs", type=int, default=1, help="--mode traffic: clustering runs captured")
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep", "slabs", "counters", "traffic"],
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "sweep", "slabs", "counters", "traffic", "tune"],
                     default="step",
                     help="step: the headline line (default); batch: fused batch vs per-instance runs; "
                          "serve: Poisson-arrival serving vs sequential runs; sweep: several minPts over one "
@@ -932,7 +984,8 @@ def main():
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
             {"batch": run_batch_mode, "serve": run_serve_mode, "sweep": run_sweep_mode,
-             "slabs": run_slabs_mode, "counters": run_counters_mode, "traffic": run_traffic_mode}[args.mode](args)
+             "slabs": run_slabs_mode, "counters": run_counters_mode, "traffic": run_traffic_mode,
+             "tune": run_tune_mode}[args.mode](args)
         return
     if world > 1:
         import torch
