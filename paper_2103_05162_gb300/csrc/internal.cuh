@@ -468,11 +468,39 @@ __device__ __forceinline__ int uf_root(const int* L, int x)
     return x;
 }
 
+// The roots of a and b (into a and b), both chains walked in the same loop
+// so that their loads overlap, with the same path halving as uf_find.
+__device__ __forceinline__ void uf_find2(int* L, int& a, int& b)
+{
+    int pa = __ldcg(L + a), pb = __ldcg(L + b);
+    while (pa != a || pb != b) {
+        const int ga = pa != a ? __ldcg(L + pa) : a;
+        const int gb = pb != b ? __ldcg(L + pb) : b;
+        if (pa != a) {
+            if (ga == pa) {
+                a = pa;  // pa is the root
+            } else {
+                __stcg(L + a, ga);
+                a = ga;
+            }
+        }
+        if (pb != b) {
+            if (gb == pb) {
+                b = pb;
+            } else {
+                __stcg(L + b, gb);
+                b = gb;
+            }
+        }
+        pa = __ldcg(L + a);
+        pb = __ldcg(L + b);
+    }
+}
+
 __device__ __forceinline__ void uf_union(int* L, int a, int b)
 {
     for (;;) {
-        a = uf_find(L, a);
-        b = uf_find(L, b);
+        uf_find2(L, a, b);
         if (a == b) return;
         if (a > b) { int t = a; a = b; b = t; }
         int old = atomicCAS(L + b, b, a);

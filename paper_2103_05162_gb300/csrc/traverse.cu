@@ -567,7 +567,11 @@ struct Rule {
     // leaf whose first point is s?
     __device__ __forceinline__ bool need_solid(int x, bool xcore, int s) const
     {
-        if (min_pts <= 2 || xcore) return uf_find(labels, x) != uf_find(labels, s);
+        if (min_pts <= 2 || xcore) {
+            int a = x, b = s;
+            uf_find2(labels, a, b);
+            return a != b;
+        }
         return claims && __ldcg(labels + x) == x;
     }
     __device__ __forceinline__ void join_solid(int x, bool xcore, int s) const
@@ -742,7 +746,11 @@ struct MainSolidV {
         const int s = r.x, e = r.y & 0x7fffffff;
         if (lsolid[L]) {
             int same = 0;
-            if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
+            if (lane == 0) {
+                int a = sQ, b = s;
+                uf_find2(rule.labels, a, b);
+                same = a == b;
+            }
             if (__shfl_sync(FULL, same, 0)) return false;
             const bool act = (mask >> lane) & 1u;
             bool found = __any_sync(FULL, act && T::far_dist2(p, box) <= e2);
@@ -843,7 +851,11 @@ struct MainBoxV {
         if (lsolid[L]) {
             // solid against solid: any adjacent cross pair unites the two sets
             int same = 0;
-            if (lane == 0) same = uf_find(rule.labels, sQ) == uf_find(rule.labels, s);
+            if (lane == 0) {
+                int a = sQ, b = s;
+                uf_find2(rule.labels, a, b);
+                same = a == b;
+            }
             if (__shfl_sync(FULL, same, 0)) return false;
             bool found = T::box_far2(qb, box) <= e2;
             // only the cell's points within eps of the other leaf's box can
