@@ -1408,8 +1408,12 @@ __global__ void k_kinds_write(const int2* __restrict__ leafr, const uint8_t* __r
     }
 }
 
-// The main phase for the leaves of one kind (KIND 0: MainPtV, 1: MainSolidV,
-// 2: MainBoxV), taken from the kind's list through a work counter.
+// The main phase (KIND 0: tiles that are not solid, MainPtV; 1: solid
+// tiles, MainSolidV; 2: dense cells larger than a tile, MainBoxV; 3: all of
+// them in one launch), taken from the kinds' lists through a work counter.
+// In one launch the dense cells come first -- few, each much work -- and the
+// warps that finish them go on to the tiles instead of leaving the GPU idle
+// until the slowest cell is done.
 template <int D, int KIND>
 __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
 {
@@ -1417,27 +1421,45 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
     WarpMem<D>* wm = reinterpret_cast<WarpMem<D>*>(smem) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t m = a.ctrl[CTRL_M];
-    uint32_t off = 0;
-    for (int t = 0; t < KIND; ++t) off += a.ctrl[CTRL_KIND_COUNT + t];
-    const int64_t cnt = a.ctrl[CTRL_KIND_COUNT + KIND];
+    const int64_t c0 = a.ctrl[CTRL_KIND_COUNT], c1 = a.ctrl[CTRL_KIND_COUNT + 1], c2 = a.ctrl[CTRL_KIND_COUNT + 2];
     // dense cells larger than a tile are few and each is much work: when
     // there are more warps than cells, up to 8 warps share a cell (split by
-    // neighbour leaf), so that the launch is not as long as its largest cell
+    // neighbour leaf), so that no warp is left with a whole large cell
     int parts = 1;
-    if (KIND == 2 && cnt > 0) {
+    if ((KIND == 2 || KIND == 3) && c2 > 0) {
         const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-        parts = (int)max((int64_t)1, min((int64_t)8, warps / cnt));
+        parts = (int)max((int64_t)1, min((int64_t)8, warps / c2));
     }
+    const int64_t n2 = (KIND == 2 || KIND == 3) ? c2 * parts : 0;
+    const int64_t total = KIND == 3 ? n2 + c1 + c0 : (KIND == 2 ? n2 : (KIND == 1 ? c1 : c0));
     for (;;) {
-        const int idx = next_leaf(&a.ctrl[CTRL_KIND_WORK + KIND]);
-        if (idx >= cnt * parts) break;
-        const int L = a.klist[off + idx / parts];
+        const int idx = next_leaf(&a.ctrl[CTRL_KIND_WORK + (KIND == 3 ? 0 : KIND)]);
+        if (idx >= total) break;
+        // the list holds kind 0, then 1, then 2
+        int kind, L, part = 0;
+        if (KIND == 3) {
+            if (idx < n2) {
+                kind = 2;
+                L = a.klist[c0 + c1 + idx / parts];
+                part = idx % parts;
+            } else if (idx < n2 + c1) {
+                kind = 1;
+                L = a.klist[c0 + (idx - n2)];
+            } else {
+                kind = 0;
+                L = a.klist[idx - n2 - c1];
+            }
+        } else {
+            kind = KIND;
+            L = a.klist[(KIND == 0 ? 0 : (KIND == 1 ? c0 : c0 + c1)) + (KIND == 2 ? idx / parts : idx)];
+            part = KIND == 2 ? idx % parts : 0;
+        }
         const TileParams tp = tile_params(a, L);
         const bool listed = a.lcap > 0 && tp.min_pts > 2;
         const Rule rule{a.labels, a.core, tp.min_pts, a.mode == DBSCAN_MODE_DBSCAN && !listed};
         const int2 r = a.leafr[L];
         const int s = r.x, e = r.y & 0x7fffffff;
-        if (KIND == 0) {
+        if (kind == 0) {
             MainPtV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.soa = &wm->soa;
             v.cbuf = wm->cbuf; v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
@@ -1455,7 +1477,7 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
                 v.qbox = warp_box<D>(v.p, v.valid);
                 walk(a, m, v, wm->stack, L);
             }
-        } else if (KIND == 1) {
+        } else if (kind == 1) {
             MainSolidV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
             v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s;
@@ -1469,7 +1491,7 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
             MainBoxV<D> v;
             v.sp = a.sp; v.leafr = a.leafr; v.lsolid = a.lsolid; v.core = a.core; v.buf = wm->buf;
             v.rule = rule; v.e2 = tp.e2; v.mask_lo = L + 1; v.lane = lane; v.sQ = s; v.eQ = e;
-            v.part = idx % parts; v.parts = parts;
+            v.part = part; v.parts = parts;
             v.qb.lo = a.nodebox[(m - 1) + L].lo;
             v.qb.hi = a.nodebox[(m - 1) + L].hi;
             walk(a, m, v, wm->stack, L);
@@ -1645,9 +1667,7 @@ void run_main(const ClusterArgs& a, cudaStream_t s)
     if (gk > 152 * 8) gk = 152 * 8;
     k_kinds_count<<<(unsigned)gk, 256, 0, s>>>(a.leafr, a.lsolid, a.ctrl);
     k_kinds_write<<<(unsigned)gk, 256, 0, s>>>(a.leafr, a.lsolid, a.ctrl, a.klist);
-    run_main_kind<D, 2>(a, s);
-    run_main_kind<D, 1>(a, s);
-    run_main_kind<D, 0>(a, s);
+    run_main_kind<D, 3>(a, s);
 }
 
 }  // namespace
@@ -1730,7 +1750,7 @@ cudaError_t launch_cluster_main(const ClusterArgs& a, cudaStream_t s)
 #define MAIN_RUN(D) run_main<D>(a, s)
     GBD_DIM_SWITCH(a.dim, MAIN_RUN)
 #undef MAIN_RUN
-    note_launches(6);
+    note_launches(4);
     return cudaGetLastError();
 }
 
