@@ -362,7 +362,7 @@ dbscan_status dbscan_last_stats(dbscan_stream stream, int64_t* stats_out);
 
 /*
  * Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
- * the 64-bit keys (8-bit digits, one decoupled look-back pass per digit;
+ * the 64-bit keys (9-bit digits, one decoupled look-back pass per digit;
  * the ordering of Morton codes in Sec. 4.1). keys/values are sorted in
  * place; n < 2^30.
  */

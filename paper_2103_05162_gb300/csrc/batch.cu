@@ -317,7 +317,7 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo, int
     p.keys_alt = c.take<uint64_t>(n);
     p.vals = c.take<uint32_t>(n);
     p.vals_alt = c.take<uint32_t>(n);
-    p.hist = c.take<uint32_t>(8 * 256);
+    p.hist = c.take<uint32_t>(SORT_MAX_PASSES * SORT_RADIX);
     p.counters = c.take<uint32_t>(8);
     p.status = c.take<uint32_t>(sort_status_words(n, 8, 64));
     p.sp = c.take<float4>(n);

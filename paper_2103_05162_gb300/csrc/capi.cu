@@ -274,7 +274,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.keys_alt = c.take<uint64_t>(n);
     p.vals = c.take<uint32_t>(n);
     p.vals_alt = c.take<uint32_t>(n);
-    p.hist = c.take<uint32_t>(8 * 256);
+    p.hist = c.take<uint32_t>(SORT_MAX_PASSES * SORT_RADIX);
     p.counters = c.take<uint32_t>(8);
     p.status = c.take<uint32_t>(sort_status_words(n, 8, 64));
     p.sp = c.take<char>(pt * (size_t)n);
@@ -1197,14 +1197,14 @@ dbscan_status dbscan_sort_pairs_u64(uint64_t* keys, uint32_t* values, int64_t n,
     Workspace* w = get_workspace(s);
     if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
     Carver c(nullptr);
-    c.take<uint64_t>(n); c.take<uint32_t>(n); c.take<uint32_t>(8 * 256); c.take<uint32_t>(8);
+    c.take<uint64_t>(n); c.take<uint32_t>(n); c.take<uint32_t>(SORT_MAX_PASSES * SORT_RADIX); c.take<uint32_t>(8);
     c.take<uint32_t>(sort_status_words(n, 8, key_bits)); c.take<uint32_t>(CTRL_WORDS);
     TRY_CUDA(ensure_arena(w->aux, c.off + 256, s));
     Carver d(w->aux.base);
     SortBuffers sb;
     sb.keys_alt = d.take<uint64_t>(n);
     sb.vals_alt = d.take<uint32_t>(n);
-    sb.hist = d.take<uint32_t>(8 * 256);
+    sb.hist = d.take<uint32_t>(SORT_MAX_PASSES * SORT_RADIX);
     sb.counters = d.take<uint32_t>(8);
     sb.status = d.take<uint32_t>(sort_status_words(n, 8, key_bits));
     uint32_t* ctrl = d.take<uint32_t>(CTRL_WORDS);

@@ -11,7 +11,13 @@ namespace gbd {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TILE = 32;  // points per non-dense BVH leaf (one warp lane per point)
-constexpr int SORT_TILE_KEYS = 256 * 16;  // keys per look-back tile of the radix sort (256 threads x 16)
+// radix sort geometry: the digit width of one pass, the digits, the most
+// passes a key takes (64-bit keys) and the keys per look-back tile (256
+// threads x 16)
+constexpr int SORT_DIGIT_BITS = 9;
+constexpr int SORT_RADIX = 1 << SORT_DIGIT_BITS;
+constexpr int SORT_MAX_PASSES = (64 + SORT_DIGIT_BITS - 1) / SORT_DIGIT_BITS;
+constexpr int SORT_TILE_KEYS = 256 * 16;
 
 // bits of the device error words
 constexpr unsigned ERR_SORT_TIMEOUT = 1u;  // a radix-sort look-back wait ran out
@@ -553,6 +559,16 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v)
 {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // float <-> order-preserving uint (for atomic min/max of floats)
 __device__ __forceinline__ uint32_t f2ord(float f)
@@ -578,8 +594,8 @@ int64_t launches_so_far();
 // ---------------------------------------------------------------------------
 
 // sort.cu
-// passes of an LSD radix sort over `bits` key bits (8-bit digits)
-__host__ __device__ __forceinline__ int sort_passes(int bits) { return (bits + 7) / 8; }
+// passes of an LSD radix sort over `bits` key bits (SORT_DIGIT_BITS-bit digits)
+__host__ __device__ __forceinline__ int sort_passes(int bits) { return (bits + SORT_DIGIT_BITS - 1) / SORT_DIGIT_BITS; }
 
 // Device-side control of a sort inside the pipeline (all null: a plain sort).
 //  * gate / gate_val: the sort runs only if *gate == gate_val (the algorithm
@@ -605,9 +621,9 @@ __host__ __device__ __forceinline__ bool sort_dev_input_alt(int host_passes, int
 struct SortBuffers {
     void* keys_alt;        // n keys
     uint32_t* vals_alt;    // n values
-    uint32_t* hist;        // 8 * 256
-    uint32_t* status;      // passes * tiles * 256
-    uint32_t* counters;    // 8
+    uint32_t* hist;        // SORT_MAX_PASSES * SORT_RADIX
+    uint32_t* status;      // passes * tiles * SORT_RADIX (8-byte aligned)
+    uint32_t* counters;    // SORT_MAX_PASSES
     uint32_t* err;         // device error word (ERR_SORT_TIMEOUT)
     SortCtl ctl;           // device-side control (pipeline sorts only)
 };

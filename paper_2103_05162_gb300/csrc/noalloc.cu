@@ -40,10 +40,10 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t OFF_KEYS = 0;
 constexpr size_t OFF_VALS = OFF_KEYS + align256(sizeof(uint64_t) * NOALLOC_MAX_PAIRS);
 constexpr size_t OFF_HIST = OFF_VALS + align256(sizeof(uint32_t) * NOALLOC_MAX_PAIRS);
-constexpr size_t OFF_COUNTERS = OFF_HIST + align256(sizeof(uint32_t) * 8 * 256);
-constexpr size_t OFF_ERR = OFF_COUNTERS + align256(sizeof(uint32_t) * 8);
+constexpr size_t OFF_COUNTERS = OFF_HIST + align256(sizeof(uint32_t) * SORT_MAX_PASSES * SORT_RADIX);
+constexpr size_t OFF_ERR = OFF_COUNTERS + align256(sizeof(uint32_t) * SORT_MAX_PASSES);
 constexpr size_t OFF_STATUS = OFF_ERR + 256;
-constexpr size_t STATUS_WORDS = (size_t)256 * NOALLOC_TILES * 8;  // 256 digits x tiles x 8 passes
+constexpr size_t STATUS_WORDS = (size_t)SORT_RADIX * NOALLOC_TILES * SORT_MAX_PASSES;  // digits x tiles x passes
 constexpr size_t NOALLOC_SCRATCH_BYTES = OFF_STATUS + align256(sizeof(uint32_t) * STATUS_WORDS);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];

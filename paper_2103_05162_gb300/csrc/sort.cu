@@ -1,6 +1,6 @@
 // Stable LSD radix sort of (key, value) pairs, onesweep style: one kernel
 // builds the digit histograms of every pass in a single read of the keys;
-// then each 8-bit pass is a single kernel in which a tile ranks its keys in
+// then each pass (one SORT_DIGIT_BITS-bit digit) is a single kernel in which a tile ranks its keys in
 // shared memory, publishes its per-digit counts, finds its global offsets by
 // decoupled look-back over the tiles before it, and scatters.
 //
@@ -25,9 +25,15 @@ namespace gbd {
 
 namespace {
 
-constexpr int THREADS = 256;  // == radix: thread t owns digit t in the per-digit steps
+constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
-constexpr int RADIX = 256;
+constexpr int DIGIT_BITS = SORT_DIGIT_BITS;
+constexpr int RADIX = SORT_RADIX;
+constexpr uint32_t DMASK = RADIX - 1;
+// digits per thread in the per-digit steps: thread t owns digits
+// [t * DPT, t * DPT + DPT), whose status words it publishes in one store
+constexpr int DPT = RADIX / THREADS;
+static_assert(DPT == 1 || DPT == 2, "one or two digits per thread");
 constexpr int ITEMS = 16;  // keys per thread (8 was measured slower despite 3 blocks per SM)
 constexpr int TILE_ITEMS = THREADS * ITEMS;
 static_assert(TILE_ITEMS == SORT_TILE_KEYS, "tile size shared with the static-scratch entry point");
@@ -58,7 +64,7 @@ template <typename K>
 __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ k0, const K* __restrict__ k1, int64_t n,
                                                   int shift0, int passes, SortCtl ctl, uint32_t* __restrict__ hist)
 {
-    __shared__ uint32_t sh[8 * RADIX];
+    __shared__ uint32_t sh[SORT_MAX_PASSES * RADIX];
     __shared__ int s_dec;
     const int pd = sort_block_passes(ctl, passes, &s_dec);
     if (pd == 0) return;
@@ -67,7 +73,7 @@ __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ k0, cons
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS) {
         K k = keys[i];
-        for (int p = 0; p < pd; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + 8 * p)) & 255u)], 1u);
+        for (int p = 0; p < pd; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + DIGIT_BITS * p)) & DMASK)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < pd * RADIX; i += THREADS) {
@@ -104,6 +110,24 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
     return r;
 }
 
+// A tile's status for the DPT digits of one thread: one relaxed store or
+// load (both halves of a 64-bit word always carry the same flag).
+__device__ __forceinline__ void st_status(uint32_t* p, const uint32_t (&w)[DPT])
+{
+    if constexpr (DPT == 1) st_relaxed(p, w[0]);
+    else st_relaxed64(reinterpret_cast<uint64_t*>(p), (uint64_t)w[0] | ((uint64_t)w[DPT - 1] << 32));
+}
+__device__ __forceinline__ void ld_status(const uint32_t* p, uint32_t (&w)[DPT])
+{
+    if constexpr (DPT == 1) {
+        w[0] = ld_relaxed(p);
+    } else {
+        const uint64_t v = ld_relaxed64(reinterpret_cast<const uint64_t*>(p));
+        w[0] = (uint32_t)v;
+        w[DPT - 1] = (uint32_t)(v >> 32);
+    }
+}
+
 // (three blocks per SM with values: the compiler then keeps every key, value
 // and rank in 80 registers without spilling, instead of taking 128 and
 // fitting two; four for keys only)
@@ -122,7 +146,7 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
     uint32_t* vals_s = reinterpret_cast<uint32_t*>(smem + TILE_ITEMS * sizeof(K));
     uint32_t* whist = reinterpret_cast<uint32_t*>(smem);  // [WARPS][RADIX], aliases keys_s
     __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_excl[RADIX];
+    __shared__ __align__(8) uint32_t s_excl[RADIX];
     __shared__ uint32_t s_gofs[RADIX];
     __shared__ uint32_t s_warp[WARPS];
     __shared__ int s_dec;
@@ -134,7 +158,7 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
     const uint32_t* __restrict__ vin = sel ? v1 : v0;
     K* __restrict__ kout = sel ? k0 : k1;
     uint32_t* __restrict__ vout = sel ? v0 : v1;
-    const int shift = shift0 + 8 * pass;
+    const int shift = shift0 + DIGIT_BITS * pass;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
@@ -163,10 +187,10 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const bool valid = (wbase + i * 32 + lane) < n;
-        const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+        const uint32_t d = (uint32_t)(k[i] >> shift) & DMASK;
         uint32_t peers = __ballot_sync(FULL, valid);
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < DIGIT_BITS; ++b) {
             const uint32_t bit = (d >> b) & 1u;
             const uint32_t m = __ballot_sync(FULL, bit);
             peers &= bit ? m : ~m;
@@ -180,29 +204,55 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
     }
     __syncthreads();
 
-    // thread tid owns digit tid: per-warp exclusive offsets and the tile count
-    uint32_t total = 0;
-    for (int w = 0; w < WARPS; ++w) {
-        uint32_t c = whist[w * RADIX + tid];
-        whist[w * RADIX + tid] = total;
-        total += c;
+    // thread tid owns digits tid * DPT + q: per-warp exclusive offsets and
+    // the tile counts
+    uint32_t total[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int dg = tid * DPT + q;
+        uint32_t t = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = whist[w * RADIX + dg];
+            whist[w * RADIX + dg] = t;
+            t += c;
+        }
+        total[q] = t;
     }
-    uint32_t* st = status + (size_t)tile * RADIX + tid;
+    uint32_t* st = status + (size_t)tile * RADIX + tid * DPT;
     const bool withhold = stall_first_tile && tile == 0;  // test hook: nothing published
-    if (!withhold) st_relaxed(st, (tile == 0 ? FLAG_PRE : FLAG_AGG) | total);
+    uint32_t word[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) word[q] = (tile == 0 ? FLAG_PRE : FLAG_AGG) | total[q];
+    if (!withhold) st_status(st, word);
 
-    const uint32_t excl = block_excl_scan(total, s_warp);
-    s_excl[tid] = excl;
-    const uint32_t dbase = block_excl_scan(hist[tid], s_warp);
+    // exclusive scans over the digits in order: the tile's own offsets and
+    // the pass's digit bases
+    uint32_t tsum = 0, hsum = 0, hv[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        hv[q] = hist[tid * DPT + q];
+        tsum += total[q];
+        hsum += hv[q];
+    }
+    uint32_t excl = block_excl_scan(tsum, s_warp);
+    uint32_t dbase = block_excl_scan(hsum, s_warp);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        s_excl[tid * DPT + q] = excl;
+        excl += total[q];
+    }
 
-    uint32_t prefix = 0;
+    uint32_t prefix[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) prefix[q] = 0;
     bool gave_up = false;
     if (tile > 0) {
         int64_t j = (int64_t)tile - 1;
         int spins = 0;
         while (j >= 0) {
-            const uint32_t s = ld_relaxed(status + (size_t)j * RADIX + tid);
-            const uint32_t flag = s & ~VAL_MASK;
+            uint32_t sw[DPT];
+            ld_status(status + (size_t)j * RADIX + tid * DPT, sw);
+            const uint32_t flag = sw[0] & ~VAL_MASK;
             if (flag == 0u) {
                 if (++spins > wait_limit) {
                     atomicOr(err, ERR_SORT_TIMEOUT);
@@ -212,15 +262,24 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
                 __nanosleep(32);
                 continue;
             }
-            prefix += s & VAL_MASK;
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) prefix[q] += sw[q] & VAL_MASK;
             if (flag == FLAG_PRE) break;
             --j;
         }
-        // a digit whose wait ran out publishes no prefix: later tiles look
+        // a tile whose wait ran out publishes no prefix: later tiles look
         // past it to the aggregates before it (or run out themselves)
-        if (!gave_up) st_relaxed(st, FLAG_PRE | ((prefix + total) & VAL_MASK));
+        if (!gave_up) {
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) word[q] = FLAG_PRE | ((prefix[q] + total[q]) & VAL_MASK);
+            st_status(st, word);
+        }
     }
-    s_gofs[tid] = dbase + prefix;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        s_gofs[tid * DPT + q] = dbase + prefix[q];
+        dbase += hv[q];
+    }
     // any digit without its offset: the tile's positions are unknown, so it
     // writes nothing
     if (__syncthreads_or(gave_up)) return;
@@ -228,7 +287,7 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
     // tile-local positions (sorted by digit, stable), then stage in shared memory
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+        const uint32_t d = (uint32_t)(k[i] >> shift) & DMASK;
         r[i] += s_excl[d] + whist[warp * RADIX + d];
     }
     __syncthreads();
@@ -244,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, VALS ? 3 : 4)
     const int cnt = rem < TILE_ITEMS ? (int)rem : TILE_ITEMS;
     for (int j = tid; j < cnt; j += THREADS) {
         const K kk = keys_s[j];
-        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        const uint32_t d = (uint32_t)(kk >> shift) & DMASK;
         const uint32_t o = s_gofs[d] + (uint32_t)j - s_excl[d];
         kout[o] = kk;
         if (VALS) vout[o] = vals_s[j];
