@@ -329,22 +329,67 @@ __global__ void k_gather(const float* __restrict__ pts, const uint32_t* __restri
         sp[i] = Traits<D>::load_point(pts, perm[i]);
 }
 
+// A 3D input point (12 bytes at float index 3j) read in aligned pieces: the
+// 16-byte block that holds it when it lies in one (one load), else an 8-byte
+// and a 4-byte piece (two loads), never past the end of the array (n points).
+// The input must be 16-byte aligned.
+__device__ __forceinline__ float4 load_point3_aligned(const float* __restrict__ pts, uint32_t j, int64_t n)
+{
+    const int64_t f = 3 * (int64_t)j;
+    const int64_t b = f & ~(int64_t)3;
+    const int o = (int)(f - b);
+    if (o == 1 || (o == 0 && b + 4 <= 3 * n)) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(pts + b));
+        return o == 0 ? make_float4(v.x, v.y, v.z, 0.0f) : make_float4(v.y, v.z, v.w, 0.0f);
+    }
+    if (o == 3) {
+        const float2 yz = __ldg(reinterpret_cast<const float2*>(pts + f + 1));
+        return make_float4(__ldg(pts + f), yz.x, yz.y, 0.0f);
+    }
+    // o == 2, or the last point of the array at o == 0
+    const float2 xy = __ldg(reinterpret_cast<const float2*>(pts + f));
+    return make_float4(xy.x, xy.y, __ldg(pts + f + 2), 0.0f);
+}
+
+template <int D, bool A16>
+__device__ __forceinline__ typename Traits<D>::Point gather_point(const float* __restrict__ pts, uint32_t j, int64_t n)
+{
+    if constexpr (D == 3 && A16) return load_point3_aligned(pts, j, n);
+    else return Traits<D>::load_point(pts, j);
+}
+
 // The same from sorted packed words, which it splits into the permutation
-// and the sorted keys.
-template <int D>
+// and the sorted keys: two sorted positions per thread and step, so that two
+// independent input reads are in flight (the words, keys and permutation are
+// 16- and 8-byte aligned workspace arrays).
+template <int D, bool A16>
 __global__ void k_gather_packed(const float* __restrict__ pts, const uint64_t* __restrict__ words, int64_t n,
                                 int idx_bits, typename Traits<D>::Point* __restrict__ sp,
                                 uint32_t* __restrict__ perm, uint64_t* __restrict__ keys,
                                 const uint32_t* __restrict__ ctrl)
 {
+    using P = typename Traits<D>::Point;
     if (!stage_on(ctrl, DBSCAN_ALGO_DENSEBOX)) return;  // (a sort that gave up: stale index bits)
     const uint64_t mask = (1ull << idx_bits) - 1ull;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pairs = n >> 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pairs; t += stride) {
+        const ulonglong2 w = reinterpret_cast<const ulonglong2*>(words)[t];
+        const uint32_t j0 = (uint32_t)(w.x & mask), j1 = (uint32_t)(w.y & mask);
+        const P p0 = gather_point<D, A16>(pts, j0, n);
+        const P p1 = gather_point<D, A16>(pts, j1, n);
+        reinterpret_cast<uint2*>(perm)[t] = make_uint2(j0, j1);
+        reinterpret_cast<ulonglong2*>(keys)[t] = make_ulonglong2(w.x >> idx_bits, w.y >> idx_bits);
+        sp[2 * t] = p0;
+        sp[2 * t + 1] = p1;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t i = n - 1;
         const uint64_t w = words[i];
         const uint32_t j = (uint32_t)(w & mask);
         perm[i] = j;
         keys[i] = w >> idx_bits;
-        sp[i] = Traits<D>::load_point(pts, j);
+        sp[i] = gather_point<D, A16>(pts, j, n);
     }
 }
 
@@ -803,10 +848,14 @@ void launch_cellkey_packed(const float* pts, int64_t n, int dim, const GridParam
 void launch_gather_packed(const float* pts, const uint64_t* words, int64_t n, int dim, int idx_bits, void* sp,
                           uint32_t* perm, uint64_t* keys, const uint32_t* ctrl, cudaStream_t s)
 {
-    const unsigned g = grid_for(n, 256, 152 * 16);
-#define GP_LAUNCH(D)                                                                                         \
-    k_gather_packed<D><<<g, 256, 0, s>>>(pts, words, n, idx_bits, static_cast<typename Traits<D>::Point*>(sp), perm, \
-                                         keys, ctrl)
+    const unsigned g = grid_for((n + 1) / 2, 256, 152 * 16);
+    const bool a16 = (reinterpret_cast<uintptr_t>(pts) & 15) == 0;
+#define GP_LAUNCH(D)                                                                                          \
+    do {                                                                                                      \
+        auto* spd = static_cast<typename Traits<D>::Point*>(sp);                                              \
+        if (a16) k_gather_packed<D, true><<<g, 256, 0, s>>>(pts, words, n, idx_bits, spd, perm, keys, ctrl);  \
+        else k_gather_packed<D, false><<<g, 256, 0, s>>>(pts, words, n, idx_bits, spd, perm, keys, ctrl);    \
+    } while (0)
     GBD_DIM_SWITCH(dim, GP_LAUNCH)
 #undef GP_LAUNCH
     note_launches(1);

@@ -71,8 +71,21 @@ __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ k0, cons
     const K* __restrict__ keys = sort_dev_input_alt(passes, pd) ? k1 : k0;
     for (int i = threadIdx.x; i < pd * RADIX; i += THREADS) sh[i] = 0;
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS) {
-        K k = keys[i];
+    // four keys per step: four independent loads in flight per thread
+    const int64_t stride = (int64_t)gridDim.x * THREADS;
+    int64_t i = blockIdx.x * (int64_t)THREADS + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        K k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = keys[i + u * stride];
+        for (int p = 0; p < pd; ++p) {
+            const int sh_p = shift0 + DIGIT_BITS * p;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) atomicAdd(&sh[p * RADIX + (uint32_t)((k[u] >> sh_p) & DMASK)], 1u);
+        }
+    }
+    for (; i < n; i += stride) {
+        const K k = keys[i];
         for (int p = 0; p < pd; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + DIGIT_BITS * p)) & DMASK)], 1u);
     }
     __syncthreads();
