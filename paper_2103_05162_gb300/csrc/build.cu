@@ -650,7 +650,18 @@ __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, c
         const bool small = l < m && e - s <= TILE;
         if (small) {
             typename T::Box b = T::empty_box();
-            for (int j = s; j < e; ++j) T::grow(b, sp[j]);
+            int j = s;
+            if constexpr (D == 3) {
+                // two 16-byte points per 256-bit load from an even index on
+                if ((j & 1) && j < e) T::grow(b, sp[j++]);
+                for (; j + 1 < e; j += 2) {
+                    float4 p0, p1;
+                    ldg256(&sp[j], p0, p1);
+                    T::grow(b, p0);
+                    T::grow(b, p1);
+                }
+            }
+            for (; j < e; ++j) T::grow(b, sp[j]);
             nodebox[(m - 1) + l] = b;
         }
         unsigned big = __ballot_sync(FULL, l < m && !small);

@@ -371,6 +371,16 @@ template <> struct Traits<3> {
     }
 };
 
+// A 32-byte record (two float4) in one 256-bit read-only load (sm_100 and
+// later); the address must be 32-byte aligned and the data read-only for the
+// kernel's lifetime.
+__device__ __forceinline__ void ldg256(const void* p, float4& x, float4& y)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w), "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+        : "l"(p));
+}
+
 template <> struct Traits<2> {
     using Point = float2;
     struct Box { float4 lo, hi; };  // z unused

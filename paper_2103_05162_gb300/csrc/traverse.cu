@@ -118,7 +118,11 @@ template <> struct NB<3> {
     __device__ static __forceinline__ T::Node load(const T::Node* n, int i)
     {
         T::Node r;
-        r.a = __ldg(&n[i].a); r.b = __ldg(&n[i].b); r.c = __ldg(&n[i].c); r.m = __ldg(&n[i].m);
+        // 64-byte records at 64-byte boundaries: two 256-bit loads
+        float4 mf;
+        ldg256(&n[i].a, r.a, r.b);
+        ldg256(&n[i].c, r.c, mf);
+        r.m = make_int4(__float_as_int(mf.x), __float_as_int(mf.y), __float_as_int(mf.z), __float_as_int(mf.w));
         return r;
     }
     __device__ static __forceinline__ T::Box box_l(const T::Node& n)
@@ -333,6 +337,17 @@ __device__ __forceinline__ void traverse_loop(const typename Traits<D>::Node* __
 
 // The traversal of one leaf's points from node `start` (an internal node,
 // or the leaf itself when it is a whole tree).
+// a node or leaf box: one 256-bit load where it is a 32-byte record (2D, 3D)
+template <int D>
+__device__ __forceinline__ typename Traits<D>::Box load_box(const typename Traits<D>::Box* __restrict__ nodebox,
+                                                            int64_t i)
+{
+    typename Traits<D>::Box b;
+    if constexpr (sizeof(typename Traits<D>::Box) == 32) ldg256(&nodebox[i], b.lo, b.hi);
+    else b = nodebox[i];
+    return b;
+}
+
 template <int D, class V>
 __device__ __forceinline__ void traverse(const typename Traits<D>::Node* __restrict__ nodes,
                                          const typename Traits<D>::Box* __restrict__ nodebox, int64_t m, V& v,
@@ -1005,7 +1020,7 @@ __global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, c
         int start = cur;
         int ns = 0;  // siblings recorded (-1: more than SIBCAP)
         int2* sib_out = a.tsib + L * SIBCAP;
-        const typename T::Box tb = a.nodebox[cur];
+        const typename T::Box tb = load_box<D>(a.nodebox, cur);
         // the depth of a tree over 64-bit keys with index tie-breaks is
         // below STACK; a longer walk means a corrupt tree: start at the root
         int steps = 0;
@@ -1018,7 +1033,7 @@ __global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, c
             }
             const int4 nm = nmeta[p];
             const int sib = nm.x == cur ? nm.y : nm.x;
-            const typename T::Box sb = a.nodebox[sib];
+            const typename T::Box sb = load_box<D>(a.nodebox, sib);
             if (box_box<D>(tb, sb) <= tp.e2) {
                 start = p;
                 if (ns >= 0 && ns < SIBCAP) {
@@ -1054,8 +1069,7 @@ __global__ void k_leaf_lists(DevArgs<D> a)
     for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < m; L += (int64_t)gridDim.x * blockDim.x) {
         const TileParams tp = tile_params(a, (int)L);
         typename T::Box q;
-        q.lo = a.nodebox[leaf0 + L].lo;
-        q.hi = a.nodebox[leaf0 + L].hi;
+        q = load_box<D>(a.nodebox, leaf0 + L);
         int32_t* out = a.llist + L * LEAFCAP;
         int cnt = 0, sp = 0;
         const int ns = a.tnsib[L];
