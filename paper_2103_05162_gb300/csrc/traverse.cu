@@ -1059,13 +1059,22 @@ __global__ void k_tile_start(DevArgs<D> a, const int32_t* __restrict__ parent, c
 // leaf lies in one of them, so the traversals of both phases can go through
 // the list instead of the tree. More than LEAFCAP leaves: count -1, and the
 // phases walk the tree for that leaf.
+// (each thread's walk stack lives in shared memory as column threadIdx.x of
+// [depth][LL_THREADS]: lanes at different depths still fall in distinct
+// banks, where a local-memory stack costs a transaction per distinct depth;
+// a walk deeper than LL_STACK gives up its list, and the phases walk the
+// tree for that leaf)
+constexpr int LL_THREADS = 256;
+constexpr int LL_STACK = 48;
+
 template <int D>
-__global__ void k_leaf_lists(DevArgs<D> a)
+__global__ void __launch_bounds__(LL_THREADS) k_leaf_lists(DevArgs<D> a)
 {
     using T = Traits<D>;
     const int64_t m = a.ctrl[CTRL_M];
     const int leaf0 = (int)(m - 1);
-    int stk[64];
+    __shared__ int s_stk[LL_STACK][LL_THREADS];
+    int* const stk = &s_stk[0][threadIdx.x];  // stk[k * LL_THREADS]: entry k
     for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < m; L += (int64_t)gridDim.x * blockDim.x) {
         const TileParams tp = tile_params(a, (int)L);
         typename T::Box q;
@@ -1079,8 +1088,8 @@ __global__ void k_leaf_lists(DevArgs<D> a)
                 if (r >= leaf0) {  // a leaf sibling: within eps of the box by construction
                     if (cnt < LEAFCAP) out[cnt] = r - leaf0;
                     ++cnt;
-                } else if (sp < 64) {
-                    stk[sp++] = r;
+                } else if (sp < LL_STACK) {
+                    stk[LL_THREADS * sp++] = r;
                 } else {
                     cnt = LEAFCAP + 1;
                 }
@@ -1095,7 +1104,7 @@ __global__ void k_leaf_lists(DevArgs<D> a)
                 cnt = LEAFCAP + 1;
                 break;
             }
-            const int node = stk[--sp];
+            const int node = stk[LL_THREADS * --sp];
             const auto nd = NB<D>::load(a.nodes, node);
             float dl, dr;
             NB<D>::bd2(nd, q, dl, dr);
@@ -1108,8 +1117,8 @@ __global__ void k_leaf_lists(DevArgs<D> a)
                         if (cnt < LEAFCAP) out[cnt] = child - leaf0;
                         ++cnt;
                     }
-                } else if (sp < 64) {
-                    stk[sp++] = child;
+                } else if (sp < LL_STACK) {
+                    stk[LL_THREADS * sp++] = child;
                 } else {
                     cnt = LEAFCAP + 1;
                 }
@@ -1727,7 +1736,7 @@ cudaError_t launch_cluster_starts(const ClusterArgs& a, cudaStream_t s)
     GBD_DIM_SWITCH(a.dim, TS_LAUNCH)
 #undef TS_LAUNCH
     if (a.llist) {
-#define LL_LAUNCH(D) k_leaf_lists<D><<<(unsigned)gm, 256, 0, s>>>(dev_args<D>(a))
+#define LL_LAUNCH(D) k_leaf_lists<D><<<(unsigned)gm, LL_THREADS, 0, s>>>(dev_args<D>(a))
         GBD_DIM_SWITCH(a.dim, LL_LAUNCH)
 #undef LL_LAUNCH
         note_launches(1);
