@@ -728,8 +728,34 @@ __global__ void k_karras(const uint64_t* __restrict__ lkey, const uint32_t* __re
 // K8: bottom-up refit. One thread per leaf climbs towards the root; at each
 // parent the first thread to arrive stops and the second, which then knows
 // both children's boxes are final, merges them (exact min/max) and writes the
-// parent's node record. No thread ever waits.
+// parent's node record. No thread ever waits. The climbing thread keeps its
+// own child's box in registers and loads only the sibling's after the
+// counter; the parent's topology (written by an earlier kernel) is read
+// before it, so one dependent load follows each counter step.
 // ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ typename Traits<D>::Box ld_box_cg(const typename Traits<D>::Box* b)
+{
+    typename Traits<D>::Box r;
+    if constexpr (sizeof(typename Traits<D>::Box) == 32) {
+        ldcg256(b, r.lo, r.hi);
+    } else {
+        r.lo = ld_cg(&b->lo);
+        r.hi = ld_cg(&b->hi);
+    }
+    return r;
+}
+template <int D>
+__device__ __forceinline__ void st_box_cg(typename Traits<D>::Box* b, const typename Traits<D>::Box& v)
+{
+    if constexpr (sizeof(typename Traits<D>::Box) == 32) {
+        stcg256(b, v.lo, v.hi);
+    } else {
+        st_cg(&b->lo, v.lo);
+        st_cg(&b->hi, v.hi);
+    }
+}
+
 template <int D>
 __global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__ parent,
                         const int4* __restrict__ nmeta, typename Traits<D>::Box* nodebox,
@@ -738,30 +764,31 @@ __global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__
     using T = Traits<D>;
     using Box = typename T::Box;
     const int64_t m = ctrl[CTRL_M];
+    if (m <= 1) return;
     uint32_t* ctrl_err = ctrl + CTRL_ERR;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
-        int64_t idx = (m - 1) + l;
-        int32_t p = m > 1 ? parent[idx] : -1;
+        int idx = (int)((m - 1) + l);
+        Box U = ld_box_cg<D>(&nodebox[idx]);  // the leaf's box (an earlier kernel's)
+        int32_t p = parent[idx];
         int depth = 0;
         while (p >= 0) {
             if (++depth > 128) {  // deeper than any valid tree: corrupt topology
                 atomicOr(&ctrl_err[0], ERR_STACK);
                 break;
             }
+            const int4 mt = nmeta[p];
+            const int32_t pp = parent[p];
             // the first of the two children to arrive stops; the second one
             // sees the first one's box (release / acquire on the counter)
             if (atomic_add_acq_rel(&visit[p], 1) == 0) break;
-            const int4 mt = nmeta[p];
-            Box L, R;
-            L.lo = ld_cg(&nodebox[mt.x].lo); L.hi = ld_cg(&nodebox[mt.x].hi);
-            R.lo = ld_cg(&nodebox[mt.y].lo); R.hi = ld_cg(&nodebox[mt.y].hi);
-            Box U = L;
-            T::merge(U, R);
-            st_cg(&nodebox[p].lo, U.lo);
-            st_cg(&nodebox[p].hi, U.hi);
+            const bool left = mt.x == idx;
+            const Box S = ld_box_cg<D>(&nodebox[left ? mt.y : mt.x]);
+            const Box L = left ? U : S, R = left ? S : U;
+            T::merge(U, S);
+            st_box_cg<D>(&nodebox[p], U);
             nodes[p] = T::make_node(L, R, mt.x, mt.y, mt.z, mt.w);
             idx = p;
-            p = parent[p];
+            p = pp;
         }
     }
 }

@@ -381,6 +381,23 @@ __device__ __forceinline__ void ldg256(const void* p, float4& x, float4& y)
         : "l"(p));
 }
 
+// The same through L2 (ld.global.cg), for records that other threads of the
+// running kernel write; volatile, so that it stays after the acquire that
+// orders it.
+__device__ __forceinline__ void ldcg256(const void* p, float4& x, float4& y)
+{
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w), "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void stcg256(void* p, const float4& x, const float4& y)
+{
+    asm volatile("st.global.cg.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(x.x), "f"(x.y), "f"(x.z),
+                 "f"(x.w), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w)
+                 : "memory");
+}
+
 template <> struct Traits<2> {
     using Point = float2;
     struct Box { float4 lo, hi; };  // z unused
