@@ -269,7 +269,10 @@ def test_tuning_does_not_change_results():
 
 def test_radix_sort_matches_stable_argsort():
     rs = np.random.default_rng(1)
-    for n, bits in ((1, 8), (4095, 12), (4097, 36), (100_000, 64), (1 << 20, 30)):
+    # key widths at and across the digit boundaries (9-bit digits: 1 to 8
+    # passes, the result in either buffer), tiles with a ragged tail
+    for n, bits in ((1, 8), (5000, 9), (5000, 10), (4095, 12), (70_001, 27), (4097, 36), (70_001, 45),
+                    (70_001, 63), (100_000, 64), (1 << 20, 30)):
         keys = rs.integers(0, 1 << min(bits, 62), size=n, dtype=np.int64)
         if bits == 64:
             keys = rs.integers(-(1 << 62), 1 << 62, size=n, dtype=np.int64)
