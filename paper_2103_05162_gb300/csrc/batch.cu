@@ -326,7 +326,7 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo, int
         p.db.pdense = c.take<uint8_t>(n);
         p.db.dstart = c.take<int32_t>(n);
     }
-    p.db.lf = c.take<int32_t>(n);
+    p.db.lf = c.take<int32_t>(n + 64);
     p.db.lidx = c.take<int32_t>(n);
     p.db.lstart = c.take<int32_t>(n + 1);
     p.db.scan_temp = c.take<int32_t>(scan_temp_words(n));

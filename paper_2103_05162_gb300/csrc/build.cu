@@ -501,8 +501,8 @@ static_assert(LEAF_T == 32, "the window holds 32 points on each side");
 
 template <typename K>
 __global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restrict__ dstart,
-                             const uint8_t* __restrict__ pdense, int64_t n, int id_shift, int32_t* __restrict__ lf,
-                             const uint32_t* __restrict__ ctrl, int algo)
+                             const uint8_t* __restrict__ pdense, int64_t n, int id_shift, uint32_t* __restrict__ lfw,
+                             int32_t* __restrict__ lfc, const uint32_t* __restrict__ ctrl, int algo)
 {
     if (!stage_on(ctrl, algo)) return;
     const int lane = threadIdx.x & 31;
@@ -578,30 +578,43 @@ __global__ void k_leaf_flags(const K* __restrict__ keys, const int32_t* __restri
                 state = (r_left + r_right + 2) > LEAF_T ? 1 : 2;
             }
         }
-        if (i >= n) continue;
-        int f;
-        if (i == 0) f = 1;
-        else if (id_shift < 64 && ((uint64_t)k1 >> id_shift) != ((uint64_t)kg >> id_shift)) f = 1;
-        else if (pdense && pdense[i] == 2) f = dstart[i] == (int32_t)i ? 1 : 0;
-        else if (pdense && pdense[i - 1] == 2) f = 1;
-        else f = state == 1 ? 1 : 0;
-        lf[i] = f;
+        bool f = false;
+        if (i >= n) f = false;
+        else if (i == 0) f = true;
+        else if (id_shift < 64 && ((uint64_t)k1 >> id_shift) != ((uint64_t)kg >> id_shift)) f = true;
+        else if (pdense && pdense[i] == 2) f = dstart[i] == (int32_t)i;
+        else if (pdense && pdense[i - 1] == 2) f = true;
+        else f = state == 1;
+        // the window's 32 flags as one word, and how many are set
+        const unsigned word = __ballot_sync(FULL, f);
+        if (lane == 0) {
+            lfw[base >> 5] = word;
+            lfc[base >> 5] = __popc(word);
+        }
     }
 }
 
-// lidx = exclusive scan of lf; writes leaf starts and m
-__global__ void k_leaf_write(const int32_t* __restrict__ lf, const int32_t* __restrict__ lidx, int64_t n,
-                             int32_t* __restrict__ lstart, uint32_t* __restrict__ ctrl, int algo)
+// Leaf starts from the flag words (bit b of word w: position 32 w + b
+// starts a leaf) and woff, the exclusive scan of their counts: one thread
+// per word writes its starts in order; the last word's thread writes m and
+// the closing entry lstart[m] = n.
+__global__ void k_leaf_write(const uint32_t* __restrict__ lfw, const int32_t* __restrict__ woff, int64_t nw,
+                             int64_t n, int32_t* __restrict__ lstart, uint32_t* __restrict__ ctrl, int algo)
 {
     // skipped (aborted run, or the other algorithm's chain): m stays 0 and
     // every later stage finds no leaves
     if (!stage_on(ctrl, algo)) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (lf[i]) lstart[lidx[i]] = (int32_t)i;
-        if (i == n - 1) {
-            const int32_t m = lidx[i] + lf[i];
-            lstart[m] = (int32_t)n;
-            ctrl[CTRL_M] = (uint32_t)m;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = lfw[w];
+        int32_t o = woff[w];
+        while (word) {
+            const int b = __ffs((int)word) - 1;
+            word &= word - 1;
+            lstart[o++] = (int32_t)(w * 32 + b);
+        }
+        if (w == nw - 1) {
+            lstart[o] = (int32_t)n;
+            ctrl[CTRL_M] = (uint32_t)o;
         }
     }
 }
@@ -918,6 +931,23 @@ void launch_gather(const float* pts, const uint32_t* perm, int64_t n, int dim, v
     note_launches(1);
 }
 
+// Leaf starts of n sorted keys into t.lstart and m into ctrl (flags as bit
+// words in t.lf, their counts after them, the counts' scan in t.lidx).
+template <typename K>
+cudaError_t launch_leaf_starts(const K* keys, const int32_t* dstart, const uint8_t* pdense, int64_t n, int id_shift,
+                               const DenseBoxTemps& t, uint32_t* ctrl, int algo, cudaStream_t s)
+{
+    const int64_t nw = (n + 31) / 32;
+    uint32_t* words = reinterpret_cast<uint32_t*>(t.lf);
+    int32_t* counts = t.lf + nw;
+    k_leaf_flags<K><<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(keys, dstart, pdense, n, id_shift, words, counts,
+                                                                ctrl, algo);
+    cudaError_t e;
+    if ((e = scan_i32(counts, t.lidx, nw, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
+    k_leaf_write<<<grid_for(nw, 256, 152 * 16), 256, 0, s>>>(words, t.lidx, nw, n, t.lstart, ctrl, algo);
+    return cudaSuccess;
+}
+
 cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t n, int dim, int min_pts, float e2,
                                    const DenseBoxTemps& t, int2* leafr, uint64_t* lkey, uint32_t* ctrl,
                                    cudaStream_t s)
@@ -932,9 +962,7 @@ cudaError_t launch_densebox_leaves(const uint64_t* keys, const void* sp, int64_t
     GBD_DIM_SWITCH(dim, DC_LAUNCH)
 #undef DC_LAUNCH
     const int A = DBSCAN_ALGO_DENSEBOX;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, 64, t.lf, ctrl, A);
-    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
+    if ((e = launch_leaf_starts<uint64_t>(keys, t.dstart, t.pdense, n, 64, t, ctrl, A, s)) != cudaSuccess) return e;
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, 64, leafr, lkey, nullptr, A);
     note_launches(4);
     return cudaGetLastError();
@@ -948,9 +976,8 @@ cudaError_t launch_batch_leaves(const uint64_t* keys, int64_t n, int id_shift, c
 {
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, t.dstart, t.pdense, n, id_shift, t.lf, ctrl, -1);
-    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, -1);
+    if ((e = launch_leaf_starts<uint64_t>(keys, t.dstart, t.pdense, n, id_shift, t, ctrl, -1, s)) != cudaSuccess)
+        return e;
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, t.pdense, keys, ctrl, id_shift, leafr, lkey, linst, -1);
     note_launches(3);
     return cudaGetLastError();
@@ -962,9 +989,7 @@ cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBox
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
     const int A = DBSCAN_ALGO_FDBSCAN;
-    k_leaf_flags<uint32_t><<<g, 256, 0, s>>>(keys32, nullptr, nullptr, n, 64, t.lf, ctrl, A);
-    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
+    if ((e = launch_leaf_starts<uint32_t>(keys32, nullptr, nullptr, n, 64, t, ctrl, A, s)) != cudaSuccess) return e;
     k_leaf_records<uint32_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys32, ctrl, 64, leafr, lkey, nullptr, A);
     note_launches(3);
     return cudaGetLastError();
@@ -976,9 +1001,7 @@ cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBox
     const unsigned g = grid_for(n, 256, 152 * 16);
     cudaError_t e;
     const int A = DBSCAN_ALGO_FDBSCAN;
-    k_leaf_flags<uint64_t><<<g, 256, 0, s>>>(keys, nullptr, nullptr, n, 64, t.lf, ctrl, A);
-    if ((e = scan_i32(t.lf, t.lidx, n, SCAN_ADD, false, t.scan_temp, s)) != cudaSuccess) return e;
-    k_leaf_write<<<g, 256, 0, s>>>(t.lf, t.lidx, n, t.lstart, ctrl, A);
+    if ((e = launch_leaf_starts<uint64_t>(keys, nullptr, nullptr, n, 64, t, ctrl, A, s)) != cudaSuccess) return e;
     k_leaf_records<uint64_t><<<g, 256, 0, s>>>(t.lstart, nullptr, keys, ctrl, 64, leafr, lkey, nullptr, A);
     note_launches(3);
     return cudaGetLastError();

@@ -104,8 +104,8 @@ cudaError_t launch_density_estimate(const float* points, int64_t n, int dim, con
 struct DenseBoxTemps {
     uint8_t* pdense;    // n: 0 not dense, 1 dense cell within a tile, 2 dense cell as its own leaf
     int32_t* dstart;    // n: first point of the dense cell (valid where pdense != 0)
-    int32_t* lf;        // n
-    int32_t* lidx;      // n
+    int32_t* lf;        // n + 64: leaf-start flags as bit words (n / 32), then their counts
+    int32_t* lidx;      // n: the counts' exclusive scan
     int32_t* lstart;    // n + 1
     int32_t* scan_temp; // scan_temp_words(n)
 };

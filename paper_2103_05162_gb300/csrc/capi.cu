@@ -284,7 +284,7 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     } else {
         p.db = DenseBoxTemps{};
     }
-    p.db.lf = c.take<int32_t>(n);
+    p.db.lf = c.take<int32_t>(n + 64);
     p.db.lidx = c.take<int32_t>(n);
     p.db.lstart = c.take<int32_t>(n + 1);
     p.db.scan_temp = c.take<int32_t>(scan_temp_words(n));
