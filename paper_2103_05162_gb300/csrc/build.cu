@@ -374,11 +374,14 @@ __global__ void k_gather_packed(const float* __restrict__ pts, const uint64_t* _
     const int64_t pairs = n >> 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pairs; t += stride) {
-        const ulonglong2 w = reinterpret_cast<const ulonglong2*>(words)[t];
+        // the words are read once and the permutation is next read by the
+        // last stages: both stream through L2 with evict-first priority, so
+        // that more of the randomly read input points stay cached
+        const ulonglong2 w = __ldcs(reinterpret_cast<const ulonglong2*>(words) + t);
         const uint32_t j0 = (uint32_t)(w.x & mask), j1 = (uint32_t)(w.y & mask);
         const P p0 = gather_point<D, A16>(pts, j0, n);
         const P p1 = gather_point<D, A16>(pts, j1, n);
-        reinterpret_cast<uint2*>(perm)[t] = make_uint2(j0, j1);
+        __stcs(reinterpret_cast<uint2*>(perm) + t, make_uint2(j0, j1));
         reinterpret_cast<ulonglong2*>(keys)[t] = make_ulonglong2(w.x >> idx_bits, w.y >> idx_bits);
         sp[2 * t] = p0;
         sp[2 * t + 1] = p1;

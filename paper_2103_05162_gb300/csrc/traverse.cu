@@ -422,6 +422,9 @@ __device__ __forceinline__ typename Traits<D>::Box warp_box(const typename Trait
     return b;
 }
 
+// the lanes of a tile of k <= 32 points
+__device__ __forceinline__ unsigned tile_lanes(int k) { return k >= 32 ? FULL : ((1u << k) - 1u); }
+
 template <int D>
 struct PreV {
     using T = Traits<D>;
@@ -1259,8 +1262,11 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_pre(DevArgs<D> a)
         v.lcap = a.lcap;
         v.qs = s;
         v.nl = 0;
-        if (__any_sync(FULL, v.act)) {
-            v.qbox = warp_box<D>(p, v.act);
+        const unsigned am = __ballot_sync(FULL, v.act);
+        if (am) {
+            // every point of the tile still counting: their box is the
+            // leaf's own (exact min/max of the same points), no reduction
+            v.qbox = am == tile_lanes(k) ? load_box<D>(a.nodebox, (m - 1) + L) : warp_box<D>(p, v.act);
             walk(a, m, v, wm->stack, L);
         }
         if (counts) {
@@ -1496,8 +1502,9 @@ __global__ void __maxnreg__(traversal_regs<D>()) k_main(DevArgs<D> a)
             v.valid = in && (tp.min_pts <= 2 || v.qcore || (rule.claims && a.nbr[v.q]));
             v.p = a.sp[in ? v.q : s];
             v.pp = NB<D>::pack(v.p);
-            if (__any_sync(FULL, v.valid)) {
-                v.qbox = warp_box<D>(v.p, v.valid);
+            const unsigned vm = __ballot_sync(FULL, v.valid);
+            if (vm) {
+                v.qbox = vm == tile_lanes(e - s) ? load_box<D>(a.nodebox, (m - 1) + L) : warp_box<D>(v.p, v.valid);
                 walk(a, m, v, wm->stack, L);
             }
         } else if (kind == 1) {
@@ -1580,7 +1587,8 @@ __global__ void k_finalize(int32_t* labels, const uint8_t* __restrict__ core, co
         const int64_t i = base + (threadIdx.x & 31);
         const bool in = i < n;
         const int r = in ? uf_find(labels, (int)i) : 0;
-        warp_atomic_min(canon, r, in ? (int32_t)perm[i] : 0, in && core[i]);
+        // (permutation and core flags are read once: evict-first)
+        warp_atomic_min(canon, r, in ? (int32_t)__ldcs(perm + i) : 0, in && __ldcs(core + i));
     }
 }
 
@@ -1593,11 +1601,15 @@ __global__ void k_relabel(const int32_t* labels, const uint8_t* __restrict__ cor
     // stale words, so nothing is written; the error is reported at the next
     // host sync point
     if (!stage_on(ctrl, -1)) return;
+    // the sequential reads (core flags, permutation, own label) stream
+    // through L2 with evict-first priority, so that the lines of the
+    // scattered output stay cached until they are complete
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool c = core[i] != 0;
-        const int r = uf_root(labels, (int)i);
+        const bool c = __ldcs(core + i) != 0;
+        int r = (int)i;
+        for (int p = __ldcs(labels + i); p != r; p = __ldcg(labels + r)) r = p;
         const bool member = c || (mode == DBSCAN_MODE_DBSCAN && r != (int)i);
-        const uint32_t o = perm[i];
+        const uint32_t o = __ldcs(perm + i);
         out[o] = member ? canon[r] : -1;
         if (core_out) core_out[o] = c ? 1 : 0;
     }
