@@ -246,6 +246,31 @@ def run_reference(args, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def timed_two_streams(gb, pts, eps, args, algo, labels, labels2, stream, s2, n, world, dev, barrier) -> dict:
+    """The timed steps with two runs in flight (alternating streams)."""
+    import torch
+    u0 = torch.cuda.Event(enable_timing=True)
+    u1 = torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    s2.wait_event(u0)
+    for i in range(args.steps):
+        gb.dbscan_run(pts, eps, args.min_pts, mode=gb.MODE_DBSCAN, algo=algo,
+                      labels_out=labels if i % 2 == 0 else labels2, stream=stream if i % 2 == 0 else s2)
+    done2 = torch.cuda.Event()
+    done2.record(s2)
+    stream.wait_event(done2)
+    u1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    gb.stream_status(stream)
+    gb.stream_status(s2)
+    ms2 = max_over_ranks(u0.elapsed_time(u1), world, dev)
+    two_streams = {"value": n * world * args.steps / (ms2 / 1e3), "unit": UNIT,
+                   "ms_per_step": ms2 / args.steps,
+                   "how": f"{args.steps} steps alternating between 2 streams, device-resident inputs, CUDA events"}
+    return two_streams
+
+
 def run_gb300(args, rank: int, world: int) -> None:
     import torch
     import torch.distributed as dist
@@ -308,23 +333,65 @@ def run_gb300(args, rank: int, world: int) -> None:
     ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     value = n * world * args.steps / (ms / 1e3)
 
-    # end to end through the host-buffer entry point: H2D of the points, the
-    # clustering, D2H of the labels, every step
-    e2e = None
+    # the same steps with two runs in flight: device-resident inputs, steps
+    # alternating between two streams (each with its own workspace), so that
+    # one run's idle phases (launch gaps, kernel tails, latency-bound stages)
+    # fill with the other's work; CUDA events on the first stream, which
+    # waits for the second before the end event
+    s2 = torch.cuda.Stream(dev)
+    labels2 = torch.empty_like(labels)
+    two_streams = None
+    for _ in range(0 if args.no_two_streams else 2):  # the second stream's workspace
+        gb.dbscan_run(pts, eps, args.min_pts, mode=gb.MODE_DBSCAN, algo=algo, labels_out=labels2, stream=s2)
+    torch.cuda.synchronize(dev)
+    gb.stream_status(s2)
+    barrier()
+    if not args.no_two_streams:
+        two_streams = timed_two_streams(gb, pts, eps, args, algo, labels, labels2, stream, s2, n, world, dev,
+                                        barrier)
+
+    # end to end through the host-buffer entry points: H2D of the points, the
+    # clustering, D2H of the labels, every step. `e2e`: the asynchronous entry
+    # point with steps alternating between two streams, so that one step's
+    # copies overlap the other's kernels (pinned host buffers, one label
+    # buffer per stream); `e2e_serial`: the synchronous entry point, one step
+    # after the other
+    e2e = e2e_serial = None
     if not args.no_e2e:
         host_pts = torch.from_numpy(X).pin_memory()
-        host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
-        hp, hl = host_pts.numpy(), host_lab.numpy()
-        for _ in range(max(1, args.warmup // 2)):
-            gb.dbscan_run_host(hp, eps, args.min_pts, algo=algo, labels_out=hl, stream=stream)
+        hp = host_pts.numpy()
+        streams = [stream, s2]
+        host_labs = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in streams]
+        hls = [t.numpy() for t in host_labs]
+        e2e_steps = max(4, args.steps // 2)
+        io = {"unit": UNIT, "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(4 * n)}
+        for k in range(2):  # each stream's workspace and staging area
+            gb.dbscan_run_host_async(hp, eps, args.min_pts, hls[k], algo=algo, stream=streams[k])
+        for st in streams:
+            st.synchronize()
+            gb.stream_status(st)
         barrier()
         te = time.perf_counter()
-        e2e_steps = max(3, args.steps // 2)
+        for i in range(e2e_steps):
+            gb.dbscan_run_host_async(hp, eps, args.min_pts, hls[i % 2], algo=algo, stream=streams[i % 2])
+        for st in streams:
+            st.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - te, world, dev)
+        for st in streams:
+            gb.stream_status(st)  # the runs' device-side status
+        e2e = {"value": n * world * e2e_steps / e2e_s, **io,
+               "how": "dbscan_run_host_async, steps alternating between 2 streams (copies of one step overlap "
+                      "the kernels of the other), pinned host buffers, wall clock from the first enqueue to "
+                      "both streams done"}
+        hl = hls[0]
+        gb.dbscan_run_host(hp, eps, args.min_pts, algo=algo, labels_out=hl, stream=stream)
+        barrier()
+        te = time.perf_counter()
         for _ in range(e2e_steps):
             gb.dbscan_run_host(hp, eps, args.min_pts, algo=algo, labels_out=hl, stream=stream)
         e2e_s = max_over_ranks(time.perf_counter() - te, world, dev)
-        e2e = {"value": n * world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
-               "d2h_bytes_per_step": int(4 * n)}
+        e2e_serial = {"value": n * world * e2e_steps / e2e_s, **io,
+                      "how": "dbscan_run_host, one step after the other (each waits for its labels)"}
 
     # roofline of the dominant stage (its kernels timed with CUDA events on the
     # launching stream over the timed region)
@@ -391,6 +458,8 @@ def run_gb300(args, rank: int, world: int) -> None:
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_serial": e2e_serial,
+            "two_streams": two_streams,
             "clocks": clocks,
             "gpu_launches": int(launches),
             "stages_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
@@ -946,6 +1015,7 @@ def main():
                     help="edge of the cube whose points form each step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-small-jobs", action="store_true", help="skip the batched / served small-job figures")
+    ap.add_argument("--no-two-streams", action="store_true", help="skip the two-runs-in-flight figure")
     ap.add_argument("--block", type=int, default=0, help="traversal block size (0: autotuner)")
     ap.add_argument("--cell-factor", type=float, default=0.0, help="DenseBox cell factor (0: autotuner)")
     ap.add_argument("--border-lists", type=int, choices=[0, 1], default=None,

@@ -122,6 +122,27 @@ dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, floa
                               dbscan_stream stream);
 
 /*
+ * dbscan_run_host without the wait (Sec. 3.2 Algorithm 3, index of Sec. 4.1
+ * or 4.2, as dbscan_run): enqueues on `stream` the copy of the points into
+ * the stream's staging area, the clustering and the copies of the labels (and
+ * core flags) into the host buffers, and returns. Host buffers must be
+ * page-locked (cudaHostAlloc, cudaHostRegister, torch pin_memory), so that
+ * the copies are asynchronous and overlap the work of other streams: steps
+ * enqueued alternately on two streams keep the host link and the kernels busy
+ * at once. The caller owns the buffers, keeps them alive and reads the
+ * results only after the stream has finished (cudaStreamSynchronize, an
+ * event, or dbscan_stream_status, which also returns the run's device-side
+ * errors, as for dbscan_run). Calls on one stream reuse its staging area in
+ * stream order. Argument errors, and pageable host buffers, are returned
+ * (DBSCAN_ERR_INVALID_ARG) before anything is enqueued; like dbscan_run, the
+ * call waits only for workspace growth and the autotuner's first call of a
+ * kind.
+ */
+dbscan_status dbscan_run_host_async(const float* points_host, int64_t n, int dim, float eps, int min_pts,
+                                    int mode, int algo, int32_t* labels_host, uint8_t* core_host,
+                                    dbscan_stream stream);
+
+/*
  * Cluster `count` independent instances in one call (the batched workload).
  *   points      device, concatenated instances; instance b is the rows
  *               offsets[b] .. offsets[b+1]-1 of dims[b] floats each, i.e. its

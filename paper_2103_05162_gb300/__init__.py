@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = [
     "DbscanError", "MODE_DBSCAN", "MODE_DBSCAN_STAR", "ALGO_FDBSCAN", "ALGO_DENSEBOX", "ALGO_AUTO",
-    "load", "library_path", "dbscan_run", "dbscan_run_host", "dbscan_run_batch", "dbscan_run_multi", "dbscan_run_slabs", "Server",
+    "load", "library_path", "dbscan_run", "dbscan_run_host", "dbscan_run_host_async", "dbscan_run_batch", "dbscan_run_multi", "dbscan_run_slabs", "Server",
     "sort_pairs_u64", "sort_pairs_u64_noalloc", "morton_codes", "lbvh_topology", "set_tuning",
     "set_auto_threshold", "last_choice", "stream_status", "release_workspaces", "profile_enable",
     "profile_collect", "kernel_launches", "last_stats",
@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True):
             "dbscan_run": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_sync": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_host": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
+            "dbscan_run_host_async": [vp, i64, i32, f32, i32, i32, i32, vp, vp, vp],
             "dbscan_run_batch": [vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp],
             "dbscan_run_multi": [vp, i64, i32, f32, vp, i32, i32, i32, vp, vp, vp],
             "dbscan_run_slabs": [vp, i64, i32, f32, i32, i32, i32, vp, vp, i64, vp],
@@ -227,6 +228,27 @@ def dbscan_run_host(points: np.ndarray, eps: float, min_pts: int, mode="dbscan",
                                _algo(algo), ctypes.c_void_p(labels_out.ctypes.data),
                                ctypes.c_void_p(core_out.ctypes.data) if core_out is not None else None,
                                _stream_handle(stream)))
+    return (labels_out, core_out) if core_out is not None else labels_out
+
+
+def dbscan_run_host_async(points: np.ndarray, eps: float, min_pts: int, labels_out: np.ndarray, mode="dbscan",
+                          algo="densebox", core_out: np.ndarray | None = None, stream=None):
+    """dbscan_run_host without the wait: enqueues copy in, clustering and
+    copy out on ``stream`` and returns. ``points``, ``labels_out`` (and
+    ``core_out``) must live in page-locked memory (e.g. the numpy view of a
+    pinned torch tensor) and stay alive until the stream is done; read them
+    after a stream synchronize or ``stream_status``."""
+    lib = load()
+    pts = np.asarray(points)
+    if pts.dtype != np.float32 or pts.ndim != 2 or not pts.flags.c_contiguous:
+        raise TypeError("points must be a C-contiguous float32 array of shape (n, dim)")
+    n, d = pts.shape
+    if labels_out.dtype != np.int32 or labels_out.shape != (n,) or not labels_out.flags.c_contiguous:
+        raise TypeError("labels_out must be a C-contiguous int32 array of n entries")
+    _check(lib.dbscan_run_host_async(ctypes.c_void_p(pts.ctypes.data), n, d, float(eps), int(min_pts), _mode(mode),
+                                     _algo(algo), ctypes.c_void_p(labels_out.ctypes.data),
+                                     ctypes.c_void_p(core_out.ctypes.data) if core_out is not None else None,
+                                     _stream_handle(stream)))
     return (labels_out, core_out) if core_out is not None else labels_out
 
 

@@ -831,6 +831,50 @@ dbscan_status prepare_single(Workspace* w, const float* points, int64_t n, int d
     return DBSCAN_OK;
 }
 
+// dbscan_run_host and dbscan_run_host_async: copy in, cluster, copy out on
+// the stream's staging area; `wait` makes it a sync point. Without the wait
+// the host buffers must be page-locked, so that the copies are asynchronous.
+bool host_pinned(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+dbscan_status run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode, int algo,
+                       int32_t* labels_host, uint8_t* core_host, dbscan_stream stream, bool wait)
+{
+    t_err.clear();
+    dbscan_status st = check_run_args(points_host, n, dim, eps, min_pts, mode, algo, labels_host);
+    if (st != DBSCAN_OK) return st;
+    if (n == 0) return DBSCAN_OK;
+    if (!wait && (!host_pinned(points_host) || !host_pinned(labels_host) || (core_host && !host_pinned(core_host))))
+        return set_error(DBSCAN_ERR_INVALID_ARG, "dbscan_run_host_async needs page-locked (pinned) host buffers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace* w = get_workspace(s);
+    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
+    const size_t pbytes = sizeof(float) * (size_t)n * dim;
+    const size_t lbytes = sizeof(int32_t) * (size_t)n;
+    const size_t io = ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)) + (size_t)n + 256;
+    TRY_CUDA(ensure_arena(w->io, io, s));
+    char* base = static_cast<char*>(w->io.base);
+    float* dpts = reinterpret_cast<float*>(base);
+    int32_t* dlab = reinterpret_cast<int32_t*>(base + ((pbytes + 255) & ~size_t(255)));
+    uint8_t* dcore = reinterpret_cast<uint8_t*>(base + ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)));
+    TRY_CUDA(cudaMemcpyAsync(dpts, points_host, pbytes, cudaMemcpyHostToDevice, s));
+    st = prepare_single(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
+    if (st != DBSCAN_OK) return st;
+    st = run_pipeline(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
+    if (st != DBSCAN_OK) return st;
+    TRY_CUDA(cudaMemcpyAsync(labels_host, dlab, lbytes, cudaMemcpyDeviceToHost, s));
+    if (core_host) TRY_CUDA(cudaMemcpyAsync(core_host, dcore, (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (!wait) return DBSCAN_OK;  // device-side errors: at the next sync point on the stream
+    return workspace_status(w, s);  // waits for the copies, then reports the run's device errors
+}
+
 }  // namespace gbd
 
 extern "C" {
@@ -905,29 +949,13 @@ dbscan_status dbscan_run_slabs(const float* points_host, int64_t n, int dim, flo
 dbscan_status dbscan_run_host(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,
                               int algo, int32_t* labels_host, uint8_t* core_host, dbscan_stream stream)
 {
-    t_err.clear();
-    dbscan_status st = check_run_args(points_host, n, dim, eps, min_pts, mode, algo, labels_host);
-    if (st != DBSCAN_OK) return st;
-    if (n == 0) return DBSCAN_OK;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Workspace* w = get_workspace(s);
-    if (!w) return set_error(DBSCAN_ERR_CUDA, "cannot create a workspace for this stream");
-    const size_t pbytes = sizeof(float) * (size_t)n * dim;
-    const size_t lbytes = sizeof(int32_t) * (size_t)n;
-    const size_t io = ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)) + (size_t)n + 256;
-    TRY_CUDA(ensure_arena(w->io, io, s));
-    char* base = static_cast<char*>(w->io.base);
-    float* dpts = reinterpret_cast<float*>(base);
-    int32_t* dlab = reinterpret_cast<int32_t*>(base + ((pbytes + 255) & ~size_t(255)));
-    uint8_t* dcore = reinterpret_cast<uint8_t*>(base + ((pbytes + 255) & ~size_t(255)) + ((lbytes + 255) & ~size_t(255)));
-    TRY_CUDA(cudaMemcpyAsync(dpts, points_host, pbytes, cudaMemcpyHostToDevice, s));
-    st = prepare_single(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
-    if (st != DBSCAN_OK) return st;
-    st = run_pipeline(w, dpts, n, dim, eps, min_pts, mode, algo, dlab, core_host ? dcore : nullptr, s);
-    if (st != DBSCAN_OK) return st;
-    TRY_CUDA(cudaMemcpyAsync(labels_host, dlab, lbytes, cudaMemcpyDeviceToHost, s));
-    if (core_host) TRY_CUDA(cudaMemcpyAsync(core_host, dcore, (size_t)n, cudaMemcpyDeviceToHost, s));
-    return workspace_status(w, s);  // waits for the copies, then reports the run's device errors
+    return run_host(points_host, n, dim, eps, min_pts, mode, algo, labels_host, core_host, stream, true);
+}
+
+dbscan_status dbscan_run_host_async(const float* points_host, int64_t n, int dim, float eps, int min_pts, int mode,
+                                    int algo, int32_t* labels_host, uint8_t* core_host, dbscan_stream stream)
+{
+    return run_host(points_host, n, dim, eps, min_pts, mode, algo, labels_host, core_host, stream, false);
 }
 
 dbscan_status dbscan_run_batch(const float* points, const int64_t* offsets, const int32_t* dims, const float* eps,

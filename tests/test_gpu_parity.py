@@ -252,6 +252,32 @@ def test_host_entry_point_matches_device_entry_point():
         assert (h_lab == d_lab).all() and (h_core.astype(bool) == d_core).all()
 
 
+def test_async_host_entry_point_on_two_streams_matches_the_oracle():
+    """dbscan_run_host_async: steps alternating between two streams, each
+    with its own pinned label buffer, give the oracle's clustering; pageable
+    host buffers are refused before anything is enqueued."""
+    X = blobs(50_000, 3, 9)
+    eps, mp = 0.02, 5
+    hx = torch.from_numpy(X).pin_memory()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for algo in ALGOS:
+        for mode in (gb.MODE_DBSCAN, gb.MODE_DBSCAN_STAR):
+            ref = oracle.dbscan(X, eps, mp, mode)
+            labs = [torch.full((X.shape[0],), -7, dtype=torch.int32).pin_memory() for _ in range(4)]
+            cores = [torch.zeros(X.shape[0], dtype=torch.uint8).pin_memory() for _ in range(4)]
+            for i in range(4):
+                gb.dbscan_run_host_async(hx.numpy(), eps, mp, labs[i].numpy(), mode=mode, algo=algo,
+                                         core_out=cores[i].numpy(), stream=streams[i % 2])
+            for st in streams:
+                st.synchronize()
+                gb.stream_status(st)
+            for i in range(4):
+                assert_matches_oracle(X, eps, mp, mode, labs[i].numpy(), cores[i].numpy(), ref=ref)
+    lab = np.empty(X.shape[0], np.int32)
+    with pytest.raises(gb.DbscanError, match="pinned"):
+        gb.dbscan_run_host_async(X, eps, mp, lab, stream=streams[0])
+
+
 def test_tuning_does_not_change_results():
     X = halos(1 << 16, 6, n_halos=200)
     eps = halo_eps(1 << 16)
