@@ -287,7 +287,8 @@ struct BatchPlan {
     void* nodes;
     int4* nmeta;
     int32_t* parent;
-    int32_t* visit;
+    int32_t* nfirst;  // first leaf of each internal node
+    void* nsum;       // block summaries of the leaf boxes
     int2* range;
     uint8_t* lsolid;
     int32_t* klist;
@@ -337,7 +338,8 @@ size_t carve_batch(BatchPlan& p, void* base, int64_t n, int count, int algo, int
     p.nodes = c.take<Traits<3>::Node>(n);
     p.nmeta = c.take<int4>(n);
     p.parent = c.take<int32_t>(2 * n);
-    p.visit = c.take<int32_t>(n);
+    p.nfirst = c.take<int32_t>(n);
+    p.nsum = c.take<Traits<3>::Box>((size_t)sum_levels_entries(n));
     p.range = c.take<int2>(n);
     p.lsolid = c.take<uint8_t>(n);
     p.klist = c.take<int32_t>(n);
@@ -424,7 +426,7 @@ cudaError_t enqueue_batch_stages(const BatchPlan& p, int64_t n, int count, int m
         note_launches(1);
     }
     if ((e = launch_batch_leaves(keys, n, lb, p.db, p.leafr, p.lkey, p.linst, p.ctrl, s)) != cudaSuccess) return e;
-    launch_lbvh(p.sp, 3, p.leafr, p.lkey, n, p.ctrl, p.nmeta, p.parent, p.visit, p.nodebox, p.nodes, s, p.range);
+    launch_lbvh(p.sp, 3, p.leafr, p.lkey, n, p.ctrl, p.nmeta, p.parent, p.nfirst, p.nodebox, p.nsum, p.nodes, s, p.range);
     k_inst_roots<<<grid_n(2 * n), 256, 0, s>>>(p.range, p.linst, p.ctrl, p.iroot);
     note_launches(1);
     // union-find init (per point instance parameters)

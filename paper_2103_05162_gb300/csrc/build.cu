@@ -646,10 +646,13 @@ __global__ void k_leaf_records(const int32_t* __restrict__ lstart, const uint8_t
 // points (reading its contiguous points in turn: few instructions per point,
 // and consecutive threads' ranges share cache lines); the leaves larger than
 // that (dense cells) are taken afterwards by the whole warp, one at a time.
+// Each warp also writes the union of its 32 leaves' boxes, the first level of
+// the block summaries that the refit reads (sum1[w]: leaves 32 w .. 32 w + 31).
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, const int2* __restrict__ leafr,
-                             const uint32_t* __restrict__ ctrl, typename Traits<D>::Box* __restrict__ nodebox)
+                             const uint32_t* __restrict__ ctrl, typename Traits<D>::Box* __restrict__ nodebox,
+                             typename Traits<D>::Box* __restrict__ sum1)
 {
     using T = Traits<D>;
     const int lane = threadIdx.x & 31;
@@ -664,6 +667,7 @@ __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, c
             e = r.y & 0x7fffffff;
         }
         const bool small = l < m && e - s <= TILE;
+        typename T::Box mine = T::empty_box();
         if (small) {
             typename T::Box b = T::empty_box();
             int j = s;
@@ -679,6 +683,7 @@ __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, c
             }
             for (; j < e; ++j) T::grow(b, sp[j]);
             nodebox[(m - 1) + l] = b;
+            mine = b;
         }
         unsigned big = __ballot_sync(FULL, l < m && !small);
         while (big) {
@@ -690,7 +695,42 @@ __global__ void k_leaf_boxes(const typename Traits<D>::Point* __restrict__ sp, c
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
             if (lane == 0) nodebox[(m - 1) + base + src] = b;
+            if (lane == src) mine = b;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) T::merge(mine, T::shfl_xor(mine, o));
+        if (lane == 0) sum1[base >> 5] = mine;
+    }
+}
+
+// Higher block summaries: level k (k >= 2) entry j is the union of level-1
+// entries [32^(k-1) j, 32^(k-1) (j + 1)), i.e. of 32^k consecutive leaves;
+// the levels follow each other in `sum` (level 1 first; sizes and count as
+// sum_level_size / sum_levels_entries). One warp per entry, reading level 1
+// directly, so no level waits for another.
+template <int D>
+__global__ void k_box_levels(const uint32_t* __restrict__ ctrl, typename Traits<D>::Box* __restrict__ sum)
+{
+    using T = Traits<D>;
+    const int lane = threadIdx.x & 31;
+    const int64_t m = ctrl[CTRL_M];
+    if (m <= 1) return;
+    const int64_t n1 = sum_level_size(m, 1);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t off = n1;   // start of level 2
+    int64_t span = 32;  // level-1 entries per entry of level k
+    for (int k = 2; k <= SUM_LEVELS && sum_level_size(m, k - 1) > SUM_DIRECT; ++k, span <<= 5) {
+        const int64_t nk = sum_level_size(m, k);
+        for (int64_t j = warp; j < nk; j += nwarps) {
+            typename T::Box b = T::empty_box();
+            const int64_t e0 = j * span, e1 = min(e0 + span, n1);
+            for (int64_t i = e0 + lane; i < e1; i += 32) T::merge(b, sum[i]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) T::merge(b, T::shfl_xor(b, o));
+            if (lane == 0) sum[off + j] = b;
+        }
+        off += nk;
     }
 }
 
@@ -709,7 +749,7 @@ __device__ __forceinline__ int kdelta(const uint64_t* __restrict__ k, int64_t m,
 
 __global__ void k_karras(const uint64_t* __restrict__ lkey, const uint32_t* __restrict__ ctrl, int64_t m_host,
                          int4* __restrict__ nmeta, int32_t* __restrict__ parent, int2* __restrict__ child_out,
-                         int2* __restrict__ range_out)
+                         int2* __restrict__ range_out, int32_t* __restrict__ first_out)
 {
     const int64_t m = m_host >= 0 ? m_host : (int64_t)ctrl[CTRL_M];
     if (blockIdx.x == 0 && threadIdx.x == 0) parent[0] = -1;  // root (or the single leaf when m == 1)
@@ -737,74 +777,116 @@ __global__ void k_karras(const uint64_t* __restrict__ lkey, const uint32_t* __re
         parent[right] = (int32_t)i;
         if (child_out) child_out[i] = make_int2(left, right);
         if (range_out) range_out[i] = make_int2((int32_t)first, (int32_t)last);
+        if (first_out) first_out[i] = (int32_t)first;
     }
 }
 
 // ---------------------------------------------------------------------------
-// K8: bottom-up refit. One thread per leaf climbs towards the root; at each
-// parent the first thread to arrive stops and the second, which then knows
-// both children's boxes are final, merges them (exact min/max) and writes the
-// parent's node record. No thread ever waits. The climbing thread keeps its
-// own child's box in registers and loads only the sibling's after the
-// counter; the parent's topology (written by an earlier kernel) is read
-// before it, so one dependent load follows each counter step.
+// K8: refit. The box of a node is the exact min/max of the boxes of the
+// leaves it covers, a contiguous range: node i covers leaves [first_i,
+// last_i], its left child [first_i, split_i] and its right child [split_i +
+// 1, last_i]. So each node's child boxes are computed directly from the leaf
+// boxes, with no dependency between nodes (no climbing, counters or fences):
+// min and max are exact in any order, so the boxes are the bottom-up ones
+// bit for bit. A node covering at most RF_SMALL leaves is done by its thread;
+// longer ranges by the whole warp, from the partial blocks at both ends of
+// each summary level and the full blocks of the next one (at most 64 loads a
+// lane per level).
 // ---------------------------------------------------------------------------
+constexpr int RF_SMALL = 32;
+
 template <int D>
-__device__ __forceinline__ typename Traits<D>::Box ld_box_cg(const typename Traits<D>::Box* b)
+__device__ __forceinline__ typename Traits<D>::Box ld_box(const typename Traits<D>::Box* b)
 {
     typename Traits<D>::Box r;
-    if constexpr (sizeof(typename Traits<D>::Box) == 32) {
-        ldcg256(b, r.lo, r.hi);
-    } else {
-        r.lo = ld_cg(&b->lo);
-        r.hi = ld_cg(&b->hi);
-    }
+    if constexpr (sizeof(typename Traits<D>::Box) == 32) ldg256(b, r.lo, r.hi);
+    else r = *b;
     return r;
 }
+
+// union of leaf boxes a..b (inclusive), by the whole warp (all lanes, same a, b)
 template <int D>
-__device__ __forceinline__ void st_box_cg(typename Traits<D>::Box* b, const typename Traits<D>::Box& v)
+__device__ typename Traits<D>::Box range_box(const typename Traits<D>::Box* __restrict__ leafbox,
+                                             const typename Traits<D>::Box* __restrict__ sum, int64_t m, int64_t a,
+                                             int64_t b, int lane)
 {
-    if constexpr (sizeof(typename Traits<D>::Box) == 32) {
-        stcg256(b, v.lo, v.hi);
-    } else {
-        st_cg(&b->lo, v.lo);
-        st_cg(&b->hi, v.hi);
+    using T = Traits<D>;
+    typename T::Box acc = T::empty_box();
+    const typename T::Box* arr = leafbox;
+    int64_t off = 0, nk = sum_level_size(m, 1);
+    for (int level = 0; a <= b && level <= SUM_LEVELS; ++level) {
+        if (b - a < SUM_DIRECT || level == SUM_LEVELS) {
+            for (int64_t j = a + lane; j <= b; j += 32) T::merge(acc, ld_box<D>(arr + j));
+            break;
+        }
+        // the partial blocks at both ends at this level, the full blocks
+        // between them at the next
+        const int64_t ha = a + lane, tb = (b & ~(int64_t)31) + lane;
+        if (ha <= (a | 31)) T::merge(acc, ld_box<D>(arr + ha));
+        if (tb <= b) T::merge(acc, ld_box<D>(arr + tb));
+        a = (a >> 5) + 1;
+        b = (b >> 5) - 1;
+        arr = sum + off;
+        off += nk;
+        nk = (nk + 31) >> 5;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) T::merge(acc, T::shfl_xor(acc, o));
+    return acc;
 }
 
 template <int D>
-__global__ void k_refit(uint32_t* __restrict__ ctrl, const int32_t* __restrict__ parent,
-                        const int4* __restrict__ nmeta, typename Traits<D>::Box* nodebox,
-                        typename Traits<D>::Node* __restrict__ nodes, int32_t* visit)
+__global__ void k_refit(uint32_t* __restrict__ ctrl, const int4* __restrict__ nmeta,
+                        const int32_t* __restrict__ nfirst, typename Traits<D>::Box* __restrict__ nodebox,
+                        const typename Traits<D>::Box* __restrict__ sum, typename Traits<D>::Node* __restrict__ nodes)
 {
     using T = Traits<D>;
     using Box = typename T::Box;
+    const int lane = threadIdx.x & 31;
     const int64_t m = ctrl[CTRL_M];
     if (m <= 1) return;
-    uint32_t* ctrl_err = ctrl + CTRL_ERR;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
-        int idx = (int)((m - 1) + l);
-        Box U = ld_box_cg<D>(&nodebox[idx]);  // the leaf's box (an earlier kernel's)
-        int32_t p = parent[idx];
-        int depth = 0;
-        while (p >= 0) {
-            if (++depth > 128) {  // deeper than any valid tree: corrupt topology
-                atomicOr(&ctrl_err[0], ERR_STACK);
-                break;
-            }
-            const int4 mt = nmeta[p];
-            const int32_t pp = parent[p];
-            // the first of the two children to arrive stops; the second one
-            // sees the first one's box (release / acquire on the counter)
-            if (atomic_add_acq_rel(&visit[p], 1) == 0) break;
-            const bool left = mt.x == idx;
-            const Box S = ld_box_cg<D>(&nodebox[left ? mt.y : mt.x]);
-            const Box L = left ? U : S, R = left ? S : U;
-            T::merge(U, S);
-            st_box_cg<D>(&nodebox[p], U);
+    const Box* leafbox = nodebox + (m - 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together (the long ranges take all lanes)
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < m - 1; base += stride) {
+        const int64_t p = base + lane;
+        int4 mt = make_int4(0, 0, 0, 0);
+        int first = 0;
+        bool ok = false;
+        if (p < m - 1) {
+            mt = nmeta[p];
+            first = nfirst[p];
+            // a range outside the leaves means a corrupt topology
+            ok = first >= 0 && first <= mt.z && mt.z < mt.w && mt.w < m;
+            if (!ok) atomicOr(&ctrl[CTRL_ERR], ERR_STACK);
+        }
+        const bool small = ok && mt.w - first < RF_SMALL;
+        if (small) {
+            Box L = T::empty_box(), R = T::empty_box();
+            int j = first;
+#pragma unroll 4
+            for (; j <= mt.z; ++j) T::merge(L, ld_box<D>(leafbox + j));
+#pragma unroll 4
+            for (; j <= mt.w; ++j) T::merge(R, ld_box<D>(leafbox + j));
+            Box U = L;
+            T::merge(U, R);
+            nodebox[p] = U;
             nodes[p] = T::make_node(L, R, mt.x, mt.y, mt.z, mt.w);
-            idx = p;
-            p = pp;
+        }
+        unsigned big = __ballot_sync(FULL, ok && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int f = __shfl_sync(FULL, first, src), g = __shfl_sync(FULL, mt.z, src),
+                      w = __shfl_sync(FULL, mt.w, src);
+            const Box L = range_box<D>(leafbox, sum, m, f, g, lane);
+            const Box R = range_box<D>(leafbox, sum, m, (int64_t)g + 1, w, lane);
+            if (lane == src) {
+                Box U = L;
+                T::merge(U, R);
+                nodebox[p] = U;
+                nodes[p] = T::make_node(L, R, mt.x, mt.y, mt.z, mt.w);
+            }
         }
     }
 }
@@ -1011,29 +1093,35 @@ cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBox
 }
 
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
-                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
+                 int4* nmeta, int32_t* parent, int32_t* nfirst, void* nodebox, void* nsum, void* nodes, cudaStream_t s,
                  int2* range_out)
 {
     const unsigned g = grid_for(m_cap, 256, 152 * 16);
-#define LB_LAUNCH(D)                                                                                         \
-    k_leaf_boxes<D><<<g, 256, 0, s>>>(static_cast<const typename Traits<D>::Point*>(sp), leafr, ctrl,         \
-                                       static_cast<typename Traits<D>::Box*>(nodebox))
+    const unsigned gl = grid_for(sum_levels_entries(m_cap) * 32, 256, 152 * 4);
+#define LB_LAUNCH(D)                                                                                           \
+    do {                                                                                                       \
+        using Bx = typename Traits<D>::Box;                                                                    \
+        k_leaf_boxes<D><<<g, 256, 0, s>>>(static_cast<const typename Traits<D>::Point*>(sp), leafr, ctrl,       \
+                                           static_cast<Bx*>(nodebox), static_cast<Bx*>(nsum));                  \
+        k_box_levels<D><<<gl, 256, 0, s>>>(ctrl, static_cast<Bx*>(nsum));                                       \
+    } while (0)
     GBD_DIM_SWITCH(dim, LB_LAUNCH)
 #undef LB_LAUNCH
-    k_karras<<<g, 256, 0, s>>>(lkey, ctrl, -1, nmeta, parent, nullptr, range_out);
-    cudaMemsetAsync(visit, 0, sizeof(int32_t) * (size_t)(m_cap > 1 ? m_cap - 1 : 1), s);
+    k_karras<<<g, 256, 0, s>>>(lkey, ctrl, -1, nmeta, parent, nullptr, range_out, nfirst);
 #define RF_LAUNCH(D)                                                                                         \
-    k_refit<D><<<g, 256, 0, s>>>(ctrl, parent, nmeta, static_cast<typename Traits<D>::Box*>(nodebox),          \
-                                 static_cast<typename Traits<D>::Node*>(nodes), visit)
+    k_refit<D><<<g, 256, 0, s>>>(ctrl, nmeta, nfirst, static_cast<typename Traits<D>::Box*>(nodebox),          \
+                                 static_cast<const typename Traits<D>::Box*>(nsum),                            \
+                                 static_cast<typename Traits<D>::Node*>(nodes))
     GBD_DIM_SWITCH(dim, RF_LAUNCH)
 #undef RF_LAUNCH
-    note_launches(3);
+    note_launches(4);
 }
 
 void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* parent, int2* child_out,
                         int2* range_out, cudaStream_t s)
 {
-    k_karras<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(lkey, nullptr, m, nmeta, parent, child_out, range_out);
+    k_karras<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(lkey, nullptr, m, nmeta, parent, child_out, range_out,
+                                                        nullptr);
     note_launches(1);
 }
 

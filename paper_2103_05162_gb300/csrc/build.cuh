@@ -191,9 +191,33 @@ cudaError_t launch_tile_leaves(const uint32_t* keys32, int64_t n, const DenseBox
                                uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
 cudaError_t launch_tile_leaves64(const uint64_t* keys, int64_t n, const DenseBoxTemps& t, int2* leafr,
                                  uint64_t* lkey, uint32_t* ctrl, cudaStream_t s);
+// Block summaries of the leaf boxes (read by the refit): level k >= 1 holds
+// ceil(m / 32^k) boxes, each the union of 32^k consecutive leaves; level
+// k + 1 exists while level k holds more than SUM_DIRECT boxes (a range of at
+// most SUM_DIRECT entries of one level is read directly).
+constexpr int SUM_LEVELS = 7;    // 32^7 leaves: beyond any leaf count
+constexpr int SUM_DIRECT = 64;
+__host__ __device__ inline int64_t sum_level_size(int64_t m, int k)
+{
+    int64_t c = m;
+    for (int i = 0; i < k; ++i) c = (c + 31) >> 5;
+    return c;
+}
+__host__ __device__ inline int64_t sum_levels_entries(int64_t m)
+{
+    int64_t t = 0, c = sum_level_size(m, 1);
+    for (int k = 1; k <= SUM_LEVELS; ++k) {
+        t += c;
+        if (c <= SUM_DIRECT) break;
+        c = (c + 31) >> 5;
+    }
+    return t;
+}
+// leaf boxes, block summaries (nsum: sum_levels_entries(m_cap) boxes),
+// Karras topology (nfirst: the first leaf of each internal node) and refit
 void launch_lbvh(const void* sp, int dim, const int2* leafr, const uint64_t* lkey, int64_t m_cap, uint32_t* ctrl,
-                 int4* nmeta, int32_t* parent, int32_t* visit, void* nodebox, void* nodes, cudaStream_t s,
-                 int2* range_out = nullptr);
+                 int4* nmeta, int32_t* parent, int32_t* nfirst, void* nodebox, void* nsum, void* nodes,
+                 cudaStream_t s, int2* range_out = nullptr);
 cudaError_t launch_batch_leaves(const uint64_t* keys, int64_t n, int id_shift, const DenseBoxTemps& t, int2* leafr,
                                 uint64_t* lkey, int32_t* linst, uint32_t* ctrl, cudaStream_t s);
 void launch_karras_only(const uint64_t* lkey, int64_t m, int4* nmeta, int32_t* parent, int2* child_out,

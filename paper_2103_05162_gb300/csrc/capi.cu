@@ -225,7 +225,8 @@ struct Plan {
     void* nodes;
     int4* nmeta;
     int32_t* parent;
-    int32_t* visit;
+    int32_t* nfirst;  // first leaf of each internal node
+    void* nsum;       // block summaries of the leaf boxes
     uint8_t* lsolid;
     int32_t* klist;
     int32_t* tstart;
@@ -294,7 +295,8 @@ size_t carve_plan(Plan& p, void* base, int64_t n, int dim, int algo, int lcap, b
     p.nodes = c.take<char>(node * (size_t)mc);
     p.nmeta = c.take<int4>(mc);
     p.parent = c.take<int32_t>(2 * mc);
-    p.visit = c.take<int32_t>(mc);
+    p.nfirst = c.take<int32_t>(mc);
+    p.nsum = c.take<char>(box * (size_t)sum_levels_entries(mc));
     p.lsolid = c.take<uint8_t>(mc);
     p.klist = c.take<int32_t>(mc);
     p.tstart = c.take<int32_t>(mc);
@@ -574,7 +576,7 @@ dbscan_status build_index(Workspace* w, const Plan& p, StageTimer& T, const floa
     }
     TRY_CUDA(cudaGetLastError());
     T.begin(ST_LBVH);
-    launch_lbvh(p.sp, dim, p.leafr, p.lkey, m_cap, p.ctrl, p.nmeta, p.parent, p.visit, p.nodebox, p.nodes, s);
+    launch_lbvh(p.sp, dim, p.leafr, p.lkey, m_cap, p.ctrl, p.nmeta, p.parent, p.nfirst, p.nodebox, p.nsum, p.nodes, s);
     T.end();
     TRY_CUDA(cudaGetLastError());
 

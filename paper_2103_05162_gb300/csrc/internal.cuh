@@ -565,16 +565,6 @@ __device__ __forceinline__ void warp_atomic_min(int32_t* a, int key, int32_t v, 
     if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(a + key, m);
 }
 
-// atomic add with acquire-release ordering at GPU scope: the writes before
-// it are visible to a thread that reads the result, and the reads after it
-// see what the threads before it wrote (in place of a fence on each side)
-__device__ __forceinline__ int atomic_add_acq_rel(int32_t* p, int v)
-{
-    int r;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
-    return r;
-}
-
 // relaxed global loads/stores for look-back status words
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p)
 {
