@@ -129,6 +129,21 @@ def test_traversal_counts_are_used_only_for_their_workload_and_sources(tmp_path)
     assert b.traversal_counts(1 << 24) is None
 
 
+def test_committed_profiles_belong_to_the_current_sources():
+    """The traversal counts and DRAM traffic that the bench line's roofline
+    reads from profiles/ were taken on the sources as they are (a kernel
+    change makes the bench drop them until they are measured again)."""
+    b = _load_bench()
+    counts = b.traversal_counts(1 << 24)
+    assert counts is not None, "profiles/ counts are stale: python bench.py --mode counters"
+    assert counts["algo"] == "densebox" and counts["min_pts"] == 10 and counts["dim"] == 3
+    per = counts["per_point"]["preprocess"]
+    assert per["distance_tests"] > 0 and per["box_tests"] > 0
+    for stage in ("preprocess", "main"):
+        t = b.measured_traffic(1 << 24, stage)
+        assert t is not None and t > 0, "profiles/ traffic is stale: retake the ncu dram__bytes capture"
+
+
 def test_fp32_operations_per_test():
     """3D: a distance test is 3 differences, 3 products and 2 sums; a box
     test 3 x (2 differences, 2 maxima, 1 product) + 2 sums."""

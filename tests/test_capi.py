@@ -159,6 +159,27 @@ def test_server_argument_errors(lib):
     assert lib.dbscan_server_poll(None, 1, None, None) == 1
 
 
+def test_async_host_entry_point_refuses_bad_arguments_and_pageable_buffers(lib):
+    """dbscan_run_host_async: argument errors, and host buffers that are not
+    page-locked (plain numpy arrays), are returned before anything is
+    enqueued."""
+    pts = np.zeros((16, 3), np.float32)
+    lab = np.zeros(16, np.int32)
+    vp = ctypes.c_void_p
+
+    def run(n, dim, eps, mp, labels=True):
+        return lib.dbscan_run_host_async(vp(pts.ctypes.data), n, dim, eps, mp, 0, 1,
+                                         vp(lab.ctypes.data) if labels else None, None, None)
+
+    assert run(16, 9, 0.1, 2) == 1
+    assert run(16, 3, 0.0, 2) == 1
+    assert run(16, 3, 0.1, 0) == 1
+    assert run(16, 3, 0.1, 2, labels=False) == 1
+    assert run(0, 3, 0.1, 2) == 0  # nothing to do
+    assert run(16, 3, 0.1, 2) == 1
+    assert b"pinned" in lib.dbscan_last_error()
+
+
 def test_component_argument_errors(lib):
     assert lib.dbscan_sort_pairs_u64(None, None, 10, 8, None) == 1
     assert lib.dbscan_sort_pairs_u64(None, None, 10, 65, None) == 1
