@@ -245,6 +245,9 @@ def dbscan_run_host_async(points: np.ndarray, eps: float, min_pts: int, labels_o
     n, d = pts.shape
     if labels_out.dtype != np.int32 or labels_out.shape != (n,) or not labels_out.flags.c_contiguous:
         raise TypeError("labels_out must be a C-contiguous int32 array of n entries")
+    if core_out is not None and (core_out.dtype != np.uint8 or core_out.shape != (n,)
+                                 or not core_out.flags.c_contiguous):
+        raise TypeError("core_out must be a C-contiguous uint8 array of n entries")
     _check(lib.dbscan_run_host_async(ctypes.c_void_p(pts.ctypes.data), n, d, float(eps), int(min_pts), _mode(mode),
                                      _algo(algo), ctypes.c_void_p(labels_out.ctypes.data),
                                      ctypes.c_void_p(core_out.ctypes.data) if core_out is not None else None,
